@@ -1,0 +1,410 @@
+"""Benchmark of the Cleora propagation path on GB300.
+
+One step = one pass of the whole path over the device-resident edge list of the workload:
+graph build (id map + CSR), init of T_0, and I propagation iterations
+(T_k = rownorm_L2(M T_{k-1})).  The metric is nnz*d/s per iteration, nnz being the CSR
+entries: nnz*d / (median per-iteration time), BF16 storage (headline) and FP32 storage.
+
+Default workload: undirected power-law graph, 41M nodes, 1.4B edges (2.8B CSR entries,
+max degree ~3M), unit weights, d = 128, I = 4, generated on the GPU.  Inputs (T: 10.5-21 GB,
+gathered bytes ~0.7-1.4 TB per iteration) are far larger than L2, so no flush is needed.
+
+Reports: roofline of the propagate kernel against the measured HBM copy bandwidth, an
+end-to-end figure through the C ABI with host buffers, the FP64 CPU oracle timed on a
+bounded sample (cpu_baseline), SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this method has) on the
+same workload family, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "large": synth.LARGE,
+    "mid": synth.MID,
+    "small": synth.SMALL,
+    # a 1/40 scale copy of the large graph (profiling and quick runs)
+    "large_1_40": synth.PowerLawSpec("chung_lu_1M_35M_undirected_d128", 1_025_000, 35_000_000,
+                                     2.0, 75_000.0, False, None, 128, 4),
+}
+
+# Bounded CPU sample of each workload for the oracle timing: same generator family, smaller.
+CPU_SAMPLES = {
+    "large": synth.PowerLawSpec("chung_lu_250k_8.5M_undirected_d128", 250_000, 8_500_000, 2.0,
+                                18_000.0, False, None, 128, 4),
+    "mid": synth.PowerLawSpec("chung_lu_200k_4M_directed_lognormal_d256", 200_000, 4_000_000, 2.1,
+                              10_000.0, True, "lognormal", 256, 4),
+    "small": synth.SMALL,
+}
+CPU_SAMPLES["large_1_40"] = CPU_SAMPLES["large"]
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def model_bytes(n, nnz, d, es, has_val):
+    """Algorithmic bytes of one iteration: rowptr and col (and val) read once, one gathered
+    row per CSR entry, every row written once."""
+    return 8 * (n + 1) + 4 * nnz + (4 * nnz if has_val else 0) + es * d * nnz + es * d * n
+
+
+def compulsory_bytes(n, nnz, d, es, has_val):
+    """Lower bound with perfect reuse: CSR once, T read once, T written once."""
+    return 8 * (n + 1) + 4 * nnz + (4 * nnz if has_val else 0) + 2 * es * d * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------------
+
+def oracle_sample_setup(workload):
+    import oracle
+    spec = CPU_SAMPLES[workload]
+    e = spec.generate()
+    g = oracle.build_from(e)
+    T0 = oracle.init(g.ids, spec.d, 0)
+    return spec, g, T0
+
+
+def oracle_iteration_rate(spec, g, T0, iters=1):
+    import oracle
+    t = time.perf_counter()
+    oracle.propagate(g, T0, iters)
+    dt = (time.perf_counter() - t) / iters
+    return g.nnz * spec.d / dt, dt
+
+
+def cpu_baseline(workload):
+    spec, g, T0 = oracle_sample_setup(workload)
+    rate, dt = oracle_iteration_rate(spec, g, T0, 1)
+    cores = os.cpu_count() or 1
+    return {"value": rate, "unit": "nnz*d/s per iteration", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, one propagation iteration of {spec.name} "
+                      f"(n={g.n}, nnz={g.nnz}, d={spec.d}; same generator family as the "
+                      f"workload, smaller), {dt:.2f} s on {cores} threads"}
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    spec, g, T0 = oracle_sample_setup(args.workload)
+    for _ in range(args.warmup):
+        oracle_iteration_rate(spec, g, T0, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_iteration_rate(spec, g, T0, 1)
+        times.append(dt)
+    dt = float(np.median(times))
+    value = g.nnz * spec.d / dt
+    cores = os.cpu_count() or 1
+    line = {
+        "impl": "reference", "metric": "nnz*d/s per iteration", "value": value,
+        "unit": "nnz*d/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload].name, "sample": spec.name,
+                   "n": g.n, "nnz": g.nnz, "d": spec.d},
+        "cpu_baseline": {"value": value, "unit": "nnz*d/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one FP64 oracle iteration per step of {spec.name} "
+                                   f"(n={g.n}, nnz={g.nnz}, d={spec.d})"},
+        "e2e": {"value": value, "unit": "nnz*d/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+def make_edges(spec, device):
+    """Device-resident edge list of the workload (src, dst int64 tensors holding uint64 ids,
+    weights or None)."""
+    import torch
+    if not spec.directed and spec.weights is None and spec.n >= 1_000_000:
+        import synth.gpu
+        src, dst, meta = synth.gpu.chung_lu_undirected(spec.n, spec.edges, spec.gamma, spec.seed,
+                                                       spec.max_deg)
+        return src, dst, None, meta
+    e = spec.generate()
+    src = torch.from_numpy(e.src.view(np.int64)).to(device)
+    dst = torch.from_numpy(e.dst.view(np.int64)).to(device)
+    w = None if e.weights is None else torch.from_numpy(e.weights).to(device)
+    return src, dst, w, e.meta
+
+
+def time_dtype(pkg, ctx, edges, spec, storage, steps, warmup, events_ok=True):
+    """Warm-up, then `steps` timed steps (build + init + I iterations), CUDA events on the
+    context's stream.  Returns per-step and per-iteration times (ms) and launch counts."""
+    import torch
+    src, dst, w, _ = edges
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(spec.iters + 3)]
+        ev[0].record(stream)
+        ctx.graph_build(src, dst, w, spec.directed)
+        ev[1].record(stream)
+        ctx.init(spec.d, 0, storage)
+        ev[2].record(stream)
+        for k in range(spec.iters):
+            ctx.propagate(1)
+            ev[3 + k].record(stream)
+        return ev
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    l0 = ctx.launches()
+    all_ev = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        all_ev.append(step(True))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = ctx.launches() - l0
+    step_ms, build_ms, init_ms, iter_ms = [], [], [], []
+    for ev in all_ev:
+        step_ms.append(ev[0].elapsed_time(ev[-1]))
+        build_ms.append(ev[0].elapsed_time(ev[1]))
+        init_ms.append(ev[1].elapsed_time(ev[2]))
+        for k in range(spec.iters):
+            iter_ms.append(ev[2 + k].elapsed_time(ev[3 + k]))
+    return {"step_ms": step_ms, "build_ms": build_ms, "init_ms": init_ms, "iter_ms": iter_ms,
+            "wall_s": wall, "launches": launches}
+
+
+def e2e_measure(pkg, spec, host_edges, storage, steps, device):
+    """Through the public API with host buffers: upload + build + init + I iterations +
+    FP32 result back to host, every step."""
+    import torch
+    src_h, dst_h, w_h = host_edges
+    with pkg.Context(device) as ctx:
+        ctx.graph_build(src_h, dst_h, w_h, spec.directed)
+        n = ctx.info()["n"]
+        out = torch.empty((n, spec.d), dtype=torch.float32, pin_memory=True)
+        times = []
+        for s in range(steps + 1):  # first one warms the pool
+            t = time.perf_counter()
+            ctx.graph_build(src_h, dst_h, w_h, spec.directed)
+            ctx.init(spec.d, 0, storage)
+            ctx.propagate(spec.iters, out)
+            ctx.sync()
+            if s > 0:
+                times.append(time.perf_counter() - t)
+    h2d = src_h.numel() * 8 * 2 + (0 if w_h is None else w_h.numel() * 4)
+    d2h = n * spec.d * 4
+    return float(np.median(times)), h2d, d2h
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--storage", default="both", choices=["both", "bf16", "f32"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2102_02302_gb300 as pkg
+
+    rank, local_rank, world = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    device = local_rank
+    spec = WORKLOADS[args.workload]
+
+    t = time.perf_counter()
+    edges = make_edges(spec, torch.device("cuda", device))
+    gen_s = time.perf_counter() - t
+
+    stream = torch.cuda.current_stream()
+    storages = ["bf16", "f32"] if args.storage == "both" else [args.storage]
+    results = {}
+    with pkg.Context(device, stream.cuda_stream) as ctx:
+        ctx.graph_build(*edges[:3], spec.directed)
+        info = ctx.info()
+        for st in storages:
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            sampler = ClockSampler(device)
+            sampler.start()
+            r = time_dtype(pkg, ctx, edges, spec, st, args.steps, args.warmup)
+            r["clocks"] = sampler.stop()
+            if world > 1:
+                tt = torch.tensor([np.mean(r["step_ms"]), np.median(r["iter_ms"])], device="cuda")
+                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+                r["max_step_ms"], r["max_iter_ms"] = float(tt[0]), float(tt[1])
+            else:
+                r["max_step_ms"], r["max_iter_ms"] = float(np.mean(r["step_ms"])), float(np.median(r["iter_ms"]))
+            results[st] = r
+
+    n, nnz, d, hv = info["n"], info["nnz"], spec.d, info["has_val"]
+    peak, peak_kind = measured_peaks()
+
+    def summary(st):
+        r = results[st]
+        es = 2 if st == "bf16" else 4
+        t_iter = r["max_iter_ms"] * 1e-3
+        mb = model_bytes(n, nnz, d, es, hv)
+        cb = compulsory_bytes(n, nnz, d, es, hv)
+        return {
+            "value": world * nnz * d / t_iter,
+            "iter_ms_median": r["max_iter_ms"],
+            "iter_ms_min": float(np.min(r["iter_ms"])),
+            "step_ms": r["max_step_ms"],
+            "build_ms": float(np.mean(r["build_ms"])),
+            "init_ms": float(np.mean(r["init_ms"])),
+            "model_bytes_per_iter": mb,
+            "compulsory_bytes_per_iter": cb,
+            "model_gbs": mb / t_iter / 1e9,
+            "compulsory_gbs": cb / t_iter / 1e9,
+            "launches": r["launches"],
+            "clocks": r["clocks"],
+            "wall_s": r["wall_s"],
+        }
+
+    sums = {st: summary(st) for st in storages}
+    head = "bf16" if "bf16" in sums else storages[0]
+    hs = sums[head]
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        src_h = edges[0].cpu().pin_memory()
+        dst_h = edges[1].cpu().pin_memory()
+        w_h = None if edges[2] is None else edges[2].cpu().pin_memory()
+        del edges
+        torch.cuda.empty_cache()
+        t_e2e, h2d, d2h = e2e_measure(pkg, spec, (src_h, dst_h, w_h), head, args.e2e_steps, device)
+        e2e = {"value": world * nnz * d * spec.iters / t_e2e, "unit": "nnz*d/s per iteration",
+               "s_per_step": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "public C ABI with pinned host buffers: edge upload, build, init, "
+                       f"{spec.iters} iterations and FP32 result download per step"}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(args.workload)
+
+    line = {
+        "metric": "nnz*d/s per iteration", "value": hs["value"], "unit": "nnz*d/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": hs["step_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": head, "data": "synthetic",
+        "config": {"workload": spec.name, "n": n, "nnz": nnz, "edges": int(info["nnz"] // 2) if not spec.directed else None,
+                   "d": d, "iters": spec.iters, "storage": head, "accumulate": "f32",
+                   "max_row_len": info["max_row_len"], "weighted": hv,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (T and gathered rows >> 129 MB); no flush",
+                   "step": "graph build + init + I iterations on device-resident edges",
+                   "value_def": "nnz*d / median per-iteration time (CUDA events)",
+                   "generator_s": gen_s},
+        "roofline": {"bound": "hbm", "achieved": hs["model_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": hs["model_gbs"] / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_model": "8(n+1) + 4nnz (+4nnz values) + s*d*nnz gathered + s*d*n written",
+                     "compulsory_gbs": hs["compulsory_gbs"],
+                     "compulsory_frac": hs["compulsory_gbs"] / peak},
+        "gpu_launches": hs["launches"],
+        "clocks": hs["clocks"],
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "breakdown": {st: {k: v for k, v in s.items() if k not in ("clocks",)} for st, s in sums.items()},
+    }
+    if "bf16" in sums and "f32" in sums:
+        line["bf16_speedup_over_f32"] = sums["f32"]["iter_ms_median"] / sums["bf16"]["iter_ms_median"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

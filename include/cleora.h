@@ -1,0 +1,147 @@
+/*
+ * cleora.h -- C ABI of the GB300 (sm_103a) Cleora propagation library.
+ *
+ * Cleora (arXiv 2102.02302) embeds a graph by iterating T_i = rownorm_L2(M T_{i-1}) with the
+ * random-walk transition matrix M = D^-1 A (Sec. 3.2, "Embedding"; Algorithm 1), starting
+ * from T_0 ~ U(-1, 1).  This library builds M on the GPU from an edge list, fills T_0 and
+ * runs the iterations with hand-written CUDA kernels.
+ *
+ * Conventions for every call:
+ *   - The return value is a cleora_status (0 = CLEORA_OK).  No C++ exception crosses the
+ *     ABI.  On failure, cleora_last_error(ctx) returns a one-line description; the context
+ *     state is unchanged unless the call says otherwise.
+ *   - Pointers are plain host or device addresses, as the matching *_on_device flag says.
+ *     Device pointers must belong to the context's device.  The caller owns every array it
+ *     passes; the library copies inputs during the call and never keeps a caller pointer.
+ *   - The library owns the graph (CSR) and embedding buffers of a context and frees them
+ *     on cleora_destroy or when a new graph is built.
+ *   - Work is ordered on the context's stream.  A call that writes to host memory returns
+ *     after the data is there.  A call that only touches device memory may return before
+ *     the GPU is done; cleora_sync waits and reports errors the kernels raised.
+ *   - State machine: create -> graph_build -> init -> propagate (repeatable).  Calls out of
+ *     order return CLEORA_ERR_STATE.
+ */
+#ifndef CLEORA_H
+#define CLEORA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cleora_ctx cleora_ctx;
+
+typedef enum {
+    CLEORA_OK = 0,
+    CLEORA_ERR_INVALID_ARG = -1, /* a size, pointer, flag or weight is out of range      */
+    CLEORA_ERR_OOM = -2,         /* device (or pinned host) memory ran out                 */
+    CLEORA_ERR_CUDA = -3,        /* a CUDA runtime call failed                             */
+    CLEORA_ERR_STATE = -4,       /* call out of order (e.g. propagate before init)         */
+    CLEORA_ERR_TIMEOUT = -5,     /* a bounded wait ran out                                 */
+    CLEORA_ERR_REJECTED = -6,    /* serving: the job can never fit the memory budget       */
+    CLEORA_ERR_DEVICE = -7       /* a kernel reported an inconsistency through its flag    */
+} cleora_status;
+
+typedef enum { CLEORA_F32 = 0, CLEORA_BF16 = 1 } cleora_dtype;
+
+/* ---------------------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t the caller
+ * owns (it must outlive the context), or NULL for a stream the context creates itself.
+ * Device memory comes from a private stream-ordered pool that keeps freed blocks for
+ * reuse; it is returned to the driver by cleora_destroy. */
+int cleora_create(cleora_ctx** out, int device, void* cuda_stream);
+void cleora_destroy(cleora_ctx* ctx);
+const char* cleora_last_error(const cleora_ctx* ctx);
+const char* cleora_status_string(int status);
+/* Waits for the context's stream; returns CLEORA_ERR_DEVICE if a kernel raised its error
+ * flag since the last check (the flag is then cleared). */
+int cleora_sync(cleora_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Graph build: node ids, CSR of M = D^-1 A (Sec. 3.2, "Embedding"; Algorithm 1, M_q)
+ * ------------------------------------------------------------------------------------- */
+
+/* Builds the transition matrix of the graph with edges src[k] -> dst[k], k < num_edges.
+ *   - Nodes are the distinct uint64 ids among src and dst; node index = rank of the id in
+ *     ascending order (so output rows follow ascending id).  At most 2^31 - 1 nodes.
+ *   - e_ab = sum of the weights of the edges a->b (weights == NULL: every weight is 1).
+ *     Undirected (directed == 0): each edge also counts as b->a (Sec. 4.5), except a
+ *     self-loop, which counts once.  Duplicates merge, their weights added as FP64 in
+ *     ascending edge order.
+ *   - deg_a = sum_b e_ab (FP64, ascending b), so every row of M sums to 1.
+ *   - Stored values: when the graph is weighted or some e_ab != 1, val[k] =
+ *     fp32(e_ab / deg_a) (FP64 division, one rounding); always inv_deg[a] = 1.0f/fp32(deg_a).
+ *   - Weights must be finite and > 0, else CLEORA_ERR_INVALID_ARG.
+ *   - num_edges == 0 gives the empty graph (n = 0); init and propagate are then no-ops.
+ * src/dst/weights are host arrays (inputs_on_device == 0) or device arrays (1).  The call
+ * returns when the graph is built.  A previous graph and its embeddings are released. */
+int cleora_graph_build(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
+                       const float* weights, int64_t num_edges, int directed,
+                       int inputs_on_device);
+int cleora_num_nodes(const cleora_ctx* ctx, int64_t* n);
+int cleora_num_entries(const cleora_ctx* ctx, int64_t* nnz);
+/* has_val: 1 when per-entry values are stored; max_deg: largest row length. */
+int cleora_graph_info(const cleora_ctx* ctx, int64_t* n, int64_t* nnz, int* has_val,
+                      int64_t* max_row_len);
+/* ids[n], ascending. */
+int cleora_node_ids(cleora_ctx* ctx, uint64_t* out, int out_on_device);
+/* Any output may be NULL.  rowptr[n+1] (int64), col[nnz] (int32, ascending in a row),
+ * val[nnz] = M_ab as FP32 (the stored value, or inv_deg[a] when no values are stored),
+ * inv_deg[n] (FP32), deg[n] (FP64). */
+int cleora_get_csr(cleora_ctx* ctx, int64_t* rowptr, int32_t* col, float* val, float* inv_deg,
+                   double* deg, int out_on_device);
+
+/* ---------------------------------------------------------------------------------------
+ * Embeddings (Sec. 3.2; Algorithm 1: initialise, then I times multiply and normalise)
+ * ------------------------------------------------------------------------------------- */
+
+/* Fills T_0 (n x d, row-major) in the storage type `storage`:
+ *   h = mix(mix(mix(seed) ^ id_i) ^ j),  T_0[i][j] = 2 * (h >> 40) * 2^-24 - 1,
+ * mix = the splitmix64 output function (add 0x9E3779B97F4A7C15, xor-shift 30, multiply
+ * 0xBF58476D1CE4E5B9, xor-shift 27, multiply 0x94D049BB133111EB, xor-shift 31).  The value
+ * is exact in FP32; BF16 storage keeps its round-to-nearest-even.  T_0 is not normalised.
+ * d must be a multiple of 8 in [8, 1024]. */
+int cleora_init(cleora_ctx* ctx, int d, uint64_t seed, cleora_dtype storage);
+
+/* Runs `iters` (>= 0) iterations T_k = rownorm_L2(M T_{k-1}) from the current embeddings:
+ *   y_a = sum_b M_ab T_{k-1}[b]  (FP32 accumulation whatever the storage type),
+ *   T_k[a] = y_a / ||y_a||_2     (FP32 norm; BF16 storage rounds to nearest even).
+ * A row with no entries (a directed sink) keeps T_{k-1}[a] / ||T_{k-1}[a]||; a row whose
+ * y is exactly zero becomes zero.  Results are deterministic (no floating-point atomics),
+ * and propagate(a) then propagate(b) equals propagate(a + b) bit for bit.
+ * If out != NULL, T_k is also written there as FP32 n x d (host or device). */
+int cleora_propagate(cleora_ctx* ctx, int iters, float* out, int out_on_device);
+/* Iterations run since init / set_embeddings. */
+int cleora_iteration(const cleora_ctx* ctx, int* k);
+/* Copies the current embeddings (n x d) out, converted to `dtype`. */
+int cleora_get_embeddings(cleora_ctx* ctx, void* out, cleora_dtype dtype, int out_on_device);
+/* Replaces the current embeddings (resume from a checkpoint); converts from `dtype` to
+ * the storage type given to init.  The iteration counter is reset to `iteration`. */
+int cleora_set_embeddings(cleora_ctx* ctx, const void* in, cleora_dtype dtype,
+                          int in_on_device, int iteration);
+
+/* ---------------------------------------------------------------------------------------
+ * Kernel schedule (autotuner hooks and counters)
+ * ------------------------------------------------------------------------------------- */
+
+typedef enum {
+    CLEORA_OPT_VEC_BYTES = 0,    /* 16 or 8: bytes per gathered vector; 0 = automatic     */
+    CLEORA_OPT_ROW_MODE = 1,     /* 0 automatic, 1 = lane groups split one row's entries,
+                                    2 = each lane group owns its own rows                 */
+    CLEORA_OPT_SPLIT_LEN = 2,    /* rows longer than this are split across warps (>= 256)  */
+    CLEORA_OPT_TASK_NNZ = 3,     /* entries per scheduled task (>= 64)                      */
+    CLEORA_OPT_BLOCKS_PER_SM = 4 /* persistent CTAs per SM; 0 = occupancy limit            */
+} cleora_option;
+int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
+int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
+/* Number of this library's kernel launches on the context so far. */
+int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLEORA_H */

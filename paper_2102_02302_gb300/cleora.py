@@ -1,0 +1,310 @@
+"""Thin ctypes binding of ``libcleora.so`` (include/cleora.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the method runs in the library's CUDA
+kernels.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA); 64-bit ids may
+be passed as uint64 or int64 (same bits).  There is no CPU fallback: if the library cannot be
+built or loaded, importing this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build_native
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_lib = None
+_lock = threading.Lock()
+
+CLEORA_OK = 0
+CLEORA_ERR_INVALID_ARG = -1
+CLEORA_ERR_OOM = -2
+CLEORA_ERR_CUDA = -3
+CLEORA_ERR_STATE = -4
+CLEORA_ERR_TIMEOUT = -5
+CLEORA_ERR_REJECTED = -6
+CLEORA_ERR_DEVICE = -7
+
+CLEORA_F32 = 0
+CLEORA_BF16 = 1
+DTYPES = {"f32": CLEORA_F32, "float32": CLEORA_F32, "bf16": CLEORA_BF16, "bfloat16": CLEORA_BF16}
+
+OPTIONS = {"vec_bytes": 0, "row_mode": 1, "split_len": 2, "task_nnz": 3, "blocks_per_sm": 4}
+
+# Every symbol include/cleora.h declares: name -> (restype, argtypes)
+SIGNATURES = {
+    "cleora_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+    "cleora_destroy": (None, [_P]),
+    "cleora_last_error": (ctypes.c_char_p, [_P]),
+    "cleora_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cleora_sync": (ctypes.c_int, [_P]),
+    "cleora_graph_build": (ctypes.c_int, [_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int]),
+    "cleora_num_nodes": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_num_entries": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_graph_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)]),
+    "cleora_node_ids": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "cleora_get_csr": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int]),
+    "cleora_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int]),
+    "cleora_propagate": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    "cleora_iteration": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "cleora_get_embeddings": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
+    "cleora_set_embeddings": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cleora_set_option": (ctypes.c_int, [_P, ctypes.c_int, _I64]),
+    "cleora_get_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64)]),
+    "cleora_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+}
+
+
+class CleoraError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return build_native.LIB
+
+
+def load(build: bool = True):
+    """Load (building first if needed) libcleora.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build_native.build() if build else build_native.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run build() first (no CPU fallback exists)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ---- pointer marshalling ----------------------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(address, on_device) of a numpy array or torch tensor (contiguous), or (None, 0)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(ctx, status: int):
+    if status != CLEORA_OK:
+        lib = load()
+        msg = lib.cleora_last_error(ctx).decode() if ctx else lib.cleora_status_string(status).decode()
+        raise CleoraError(status, msg or lib.cleora_status_string(status).decode())
+
+
+# ---- the C functions, one Python function each --------------------------------------------
+
+def cleora_create(device: int = 0, stream: int | None = None):
+    lib = load()
+    h = _P()
+    st = lib.cleora_create(ctypes.byref(h), device, stream)
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_create failed: " + lib.cleora_status_string(st).decode())
+    return h
+
+
+def cleora_destroy(ctx) -> None:
+    load().cleora_destroy(ctx)
+
+
+def cleora_last_error(ctx) -> str:
+    return load().cleora_last_error(ctx).decode()
+
+
+def cleora_sync(ctx) -> None:
+    _check(ctx, load().cleora_sync(ctx))
+
+
+def cleora_graph_build(ctx, src, dst, weights=None, directed: bool = False) -> None:
+    ps, ds = _ptr(src)
+    pd, dd = _ptr(dst)
+    pw, dw = _ptr(weights)
+    n_edges = int(src.shape[0])
+    if int(dst.shape[0]) != n_edges or (weights is not None and int(weights.shape[0]) != n_edges):
+        raise ValueError("src, dst and weights must have the same length")
+    on_dev = ds
+    if dd != on_dev or (weights is not None and dw != on_dev):
+        raise ValueError("src, dst and weights must all be on the host or all on the device")
+    _check(ctx, load().cleora_graph_build(ctx, ps, pd, pw, n_edges, int(bool(directed)), on_dev))
+
+
+def cleora_num_nodes(ctx) -> int:
+    v = _I64()
+    _check(ctx, load().cleora_num_nodes(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def cleora_num_entries(ctx) -> int:
+    v = _I64()
+    _check(ctx, load().cleora_num_entries(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def cleora_graph_info(ctx) -> dict:
+    n, nnz, mx = _I64(), _I64(), _I64()
+    hv = ctypes.c_int()
+    _check(ctx, load().cleora_graph_info(ctx, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(hv),
+                                         ctypes.byref(mx)))
+    return {"n": n.value, "nnz": nnz.value, "has_val": bool(hv.value), "max_row_len": mx.value}
+
+
+def cleora_node_ids(ctx, out) -> None:
+    p, dev = _ptr(out)
+    _check(ctx, load().cleora_node_ids(ctx, p, dev))
+
+
+def cleora_get_csr(ctx, rowptr=None, col=None, val=None, inv_deg=None, deg=None) -> None:
+    ptrs = [_ptr(x) for x in (rowptr, col, val, inv_deg, deg)]
+    devs = {d for (p, d) in ptrs if p is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be on the host or all on the device")
+    dev = devs.pop() if devs else 0
+    _check(ctx, load().cleora_get_csr(ctx, *[p for p, _ in ptrs], dev))
+
+
+def cleora_init(ctx, d: int, seed: int = 0, storage: str | int = "f32") -> None:
+    dt = DTYPES[storage] if isinstance(storage, str) else int(storage)
+    _check(ctx, load().cleora_init(ctx, int(d), int(seed) & (2**64 - 1), dt))
+
+
+def cleora_propagate(ctx, iters: int, out=None) -> None:
+    p, dev = _ptr(out)
+    _check(ctx, load().cleora_propagate(ctx, int(iters), p, dev))
+
+
+def cleora_iteration(ctx) -> int:
+    v = ctypes.c_int()
+    _check(ctx, load().cleora_iteration(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def cleora_get_embeddings(ctx, out, dtype: str | int = "f32") -> None:
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    p, dev = _ptr(out)
+    _check(ctx, load().cleora_get_embeddings(ctx, p, dt, dev))
+
+
+def cleora_set_embeddings(ctx, inp, dtype: str | int = "f32", iteration: int = 0) -> None:
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    p, dev = _ptr(inp)
+    _check(ctx, load().cleora_set_embeddings(ctx, p, dt, dev, int(iteration)))
+
+
+def cleora_set_option(ctx, name: str, value: int) -> None:
+    _check(ctx, load().cleora_set_option(ctx, OPTIONS[name], int(value)))
+
+
+def cleora_get_option(ctx, name: str) -> int:
+    v = _I64()
+    _check(ctx, load().cleora_get_option(ctx, OPTIONS[name], ctypes.byref(v)))
+    return v.value
+
+
+def cleora_launch_count(ctx) -> int:
+    v = _I64()
+    _check(ctx, load().cleora_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+# ---- convenience object (same calls, owns the handle) ------------------------------------
+
+class Context:
+    """One graph and its embeddings on one GPU; wraps a ``cleora_ctx``."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.handle = cleora_create(device, stream)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cleora_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def graph_build(self, src, dst, weights=None, directed=False):
+        cleora_graph_build(self.handle, src, dst, weights, directed)
+        return self
+
+    def info(self) -> dict:
+        return cleora_graph_info(self.handle)
+
+    def node_ids(self) -> np.ndarray:
+        out = np.empty(cleora_num_nodes(self.handle), np.uint64)
+        cleora_node_ids(self.handle, out)
+        return out
+
+    def csr(self) -> dict:
+        inf = self.info()
+        n, nnz = inf["n"], inf["nnz"]
+        r = {"rowptr": np.empty(n + 1, np.int64), "col": np.empty(nnz, np.int32),
+             "val": np.empty(nnz, np.float32), "inv_deg": np.empty(n, np.float32),
+             "deg": np.empty(n, np.float64)}
+        cleora_get_csr(self.handle, r["rowptr"], r["col"], r["val"], r["inv_deg"], r["deg"])
+        r.update(inf)
+        return r
+
+    def init(self, d, seed=0, storage="f32"):
+        cleora_init(self.handle, d, seed, storage)
+        self.d = d
+        self.storage = storage
+        return self
+
+    def propagate(self, iters, out=None):
+        cleora_propagate(self.handle, iters, out)
+        return out
+
+    def embeddings(self, dtype="f32"):
+        n = cleora_num_nodes(self.handle)
+        if dtype == "f32":
+            out = np.empty((n, self.d), np.float32)
+        else:
+            out = np.empty((n, self.d), np.uint16)  # raw bf16 bits
+        cleora_get_embeddings(self.handle, out, dtype)
+        return out
+
+    def set_embeddings(self, arr, dtype="f32", iteration=0):
+        cleora_set_embeddings(self.handle, arr, dtype, iteration)
+
+    def set_option(self, name, value):
+        cleora_set_option(self.handle, name, value)
+
+    def sync(self):
+        cleora_sync(self.handle)
+
+    def launches(self) -> int:
+        return cleora_launch_count(self.handle)

@@ -1,0 +1,145 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "cleora.h"
+
+namespace cleora {
+
+// A scheduled unit of propagation work (16 bytes).
+//   normal task : rows [a, b) processed whole;              c = -1, k = 0
+//   split chunk : entries [c * len, (c+1) * len) of row a;  b = split-row index, k = chunks
+struct Task {
+    int32_t a, b, c, k;
+};
+
+// Work list of one graph for one schedule (split length and task size).
+struct Plan {
+    bool valid = false;
+    int64_t split_len = 0, task_nnz = 0;
+    int64_t ntasks = 0;        // split chunks first, then normal tasks
+    int64_t nsplit_rows = 0;   // rows split across warps
+    int64_t nsplit_chunks = 0; // = number of partial-sum slots
+    Task* tasks = nullptr;
+    int64_t* split_base = nullptr;  // per split row: its first partial slot
+    int32_t* split_count = nullptr; // per split row: arrival counter, reset by the last warp
+    unsigned long long* counter = nullptr;  // dynamic task counter (zeroed per launch)
+    float* partials = nullptr;      // nsplit_chunks x d FP32 partial sums
+    int64_t partials_d = 0;
+};
+
+struct Graph {
+    bool built = false;
+    int64_t n = 0, nnz = 0, max_row_len = 0;
+    bool has_val = false;
+    uint64_t* ids = nullptr;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    float* val = nullptr;      // nnz, only when has_val
+    float* inv_deg = nullptr;  // n
+    double* deg = nullptr;     // n
+};
+
+// Kernel shape for one (d, storage) pair.
+struct Shape {
+    int vec = 16;   // bytes per gathered vector
+    int G = 32;     // lanes that cover one row of T
+    int cpl = 1;    // vectors per lane per row
+    int mode = 1;   // 1: lane groups split a row's entries, 2: each group owns rows
+    int chunks = 0; // vectors per row
+};
+
+enum { OPT_COUNT = 5 };
+
+}  // namespace cleora
+
+struct cleora_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaMemPool_t pool = nullptr;
+    int num_sms = 0;
+    std::string err;
+
+    cleora::Graph g;
+    cleora::Plan plan;
+
+    bool inited = false;
+    int d = 0;
+    cleora_dtype dtype = CLEORA_F32;
+    void* T[2] = {nullptr, nullptr};
+    int cur = 0;
+    int iteration = 0;
+
+    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0};
+    int* err_flag = nullptr;  // device int, raised by kernels
+    int64_t launches = 0;
+};
+
+namespace cleora {
+
+// ---- error plumbing ------------------------------------------------------------------
+int fail(cleora_ctx* ctx, int status, const char* fmt, ...);
+int cuda_fail(cleora_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+
+#define CL_CUDA(ctx, call)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) return ::cleora::cuda_fail(ctx, e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define CL_LAUNCHED(ctx)                                                            \
+    do {                                                                            \
+        (ctx)->launches += 1;                                                       \
+        cudaError_t e_ = cudaGetLastError();                                        \
+        if (e_ != cudaSuccess) return ::cleora::cuda_fail(ctx, e_, "kernel launch", __FILE__, __LINE__); \
+    } while (0)
+
+#define CL_TRY(x)                      \
+    do {                               \
+        int s_ = (x);                  \
+        if (s_ != CLEORA_OK) return s_; \
+    } while (0)
+
+// ---- stream-ordered device memory from the context's pool ----------------------------
+int dalloc_bytes(cleora_ctx* ctx, void** p, size_t bytes);
+template <class T>
+inline int dalloc(cleora_ctx* ctx, T** p, size_t count) {
+    return dalloc_bytes(ctx, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+void dfree(cleora_ctx* ctx, void* p);
+template <class T>
+inline void dfree_null(cleora_ctx* ctx, T*& p) {
+    dfree(ctx, p);
+    p = nullptr;
+}
+
+inline unsigned grid_for(int64_t items, int threads, int num_sms) {
+    int64_t b = (items + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 32;
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---- parts implemented in the other translation units --------------------------------
+int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
+                     const float* w, int64_t E, int directed);
+void graph_release(cleora_ctx* ctx);
+int csr_values_out(cleora_ctx* ctx, float* val_dev);  // M_ab per entry as FP32
+
+int init_impl(cleora_ctx* ctx, uint64_t seed);
+int convert_impl(cleora_ctx* ctx, const void* src, cleora_dtype sdt, void* dst, cleora_dtype ddt,
+                 int64_t count);
+
+Shape choose_shape(const cleora_ctx* ctx, int d, cleora_dtype dt);
+int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz);
+void plan_release(cleora_ctx* ctx);
+int plan_ensure(cleora_ctx* ctx);
+int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout);
+
+}  // namespace cleora

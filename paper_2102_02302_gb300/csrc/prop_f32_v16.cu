@@ -1,0 +1,14 @@
+// Propagate kernels instantiated for storage type float and 16-byte gathers.
+#include "propagate_kernels.cuh"
+
+namespace cleora {
+namespace prop {
+
+cudaError_t launch_f32_v16(const Shape& sh, const Args& a, bool hv, int bps, int sms, cudaStream_t s,
+                      int* grid) {
+    return hv ? Launch<float, 16, true>::run(sh, a, bps, sms, s, grid)
+              : Launch<float, 16, false>::run(sh, a, bps, sms, s, grid);
+}
+
+}  // namespace prop
+}  // namespace cleora

@@ -1,0 +1,265 @@
+// Host side of one Cleora iteration (arXiv 2102.02302, Algorithm 1, inner loop): kernel
+// shape for (d, storage), the task plan of a graph, and the launch.
+//
+// Plan.  Rows longer than `split_len` entries are split into chunks of `split_len`; every
+// other row belongs to a run of consecutive rows.  A new run starts where
+// floor((rowptr[r] + ROW_COST * r) / task_nnz) changes, so runs hold about task_nnz entries
+// (rows without entries still cost ROW_COST).  Tasks are ordered longest first: all split
+// chunks, then the runs in row order.  The plan is built on the device and depends only on
+// the graph and the two sizes, never on timing, so the summation order of every row is
+// fixed by the graph's shape.
+#include <cub/device/device_scan.cuh>
+#include <cub/device/device_select.cuh>
+#include <thrust/iterator/counting_iterator.h>
+
+#include "propagate_kernels.cuh"
+
+namespace cleora {
+namespace {
+
+constexpr int64_t ROW_COST = 8;
+constexpr int64_t DEFAULT_SPLIT_LEN = 8192;
+constexpr int64_t DEFAULT_TASK_NNZ = 4096;
+
+__device__ __forceinline__ int64_t run_key(const int64_t* rowptr, int64_t r, int64_t task_nnz) {
+    return (rowptr[r] + ROW_COST * r) / task_nnz;
+}
+
+__global__ void k_plan_mark(const int64_t* rowptr, int64_t n, int64_t split_len, int64_t task_nnz,
+                            uint8_t* brk) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const bool split = rowptr[r + 1] - rowptr[r] > split_len;
+        bool b = split || r == 0;
+        if (!b) {
+            const bool prev_split = rowptr[r] - rowptr[r - 1] > split_len;
+            b = prev_split || run_key(rowptr, r, task_nnz) != run_key(rowptr, r - 1, task_nnz);
+        }
+        brk[r] = b ? 1 : 0;
+    }
+}
+
+// Per break i: chunks (split rows), normal-task flag and split flag.
+__global__ void k_plan_counts(const int64_t* rowptr, const int32_t* brk_rows, int64_t nb,
+                              int64_t split_len, int64_t* chunks, int64_t* normal, int64_t* split) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = brk_rows[i];
+        const int64_t len = rowptr[r + 1] - rowptr[r];
+        const bool s = len > split_len;
+        chunks[i] = s ? (len + split_len - 1) / split_len : 0;
+        normal[i] = s ? 0 : 1;
+        split[i] = s ? 1 : 0;
+    }
+}
+
+__global__ void k_plan_fill(const int32_t* brk_rows, int64_t nb, int64_t n, const int64_t* chunks,
+                            const int64_t* cbase, const int64_t* nbase, const int64_t* sbase,
+                            int64_t total_chunks, Task* tasks, int64_t* split_base) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = brk_rows[i];
+        const int64_t nc = chunks[i];
+        if (nc > 0) {
+            const int64_t sidx = sbase[i];
+            split_base[sidx] = cbase[i];
+            for (int64_t c = 0; c < nc; ++c) {
+                Task t;
+                t.a = r;
+                t.b = (int32_t)sidx;
+                t.c = (int32_t)c;
+                t.k = (int32_t)nc;
+                tasks[cbase[i] + c] = t;
+            }
+        } else {
+            Task t;
+            t.a = r;
+            t.b = (int32_t)((i + 1 < nb) ? (int64_t)brk_rows[i + 1] : n);
+            t.c = -1;
+            t.k = 0;
+            tasks[total_chunks + nbase[i]] = t;
+        }
+    }
+}
+
+int pow2ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+Shape choose_shape(const cleora_ctx* ctx, int d, cleora_dtype dt) {
+    Shape sh;
+    const int es = dt == CLEORA_F32 ? 4 : 2;
+    int vec = ctx->opt[CLEORA_OPT_VEC_BYTES] == 8 ? 8 : 16;
+    int chunks = d * es / vec;
+    if (vec == 8 && pow2ceil((chunks + 31) / 32) > 8) {  // too many vectors per lane
+        vec = 16;
+        chunks = d * es / vec;
+    }
+    sh.vec = vec;
+    sh.chunks = chunks;
+    if (chunks <= 32) {
+        sh.G = pow2ceil(chunks);
+        sh.cpl = 1;
+    } else {
+        sh.G = 32;
+        sh.cpl = pow2ceil((chunks + 31) / 32);
+    }
+    const int64_t m = ctx->opt[CLEORA_OPT_ROW_MODE];
+    sh.mode = (m == 2 && sh.G < 32) ? 2 : 1;
+    return sh;
+}
+
+void plan_release(cleora_ctx* ctx) {
+    Plan& p = ctx->plan;
+    dfree_null(ctx, p.tasks);
+    dfree_null(ctx, p.split_base);
+    dfree_null(ctx, p.split_count);
+    dfree_null(ctx, p.counter);
+    dfree_null(ctx, p.partials);
+    p = Plan();
+}
+
+int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz) {
+    plan_release(ctx);
+    const Graph& g = ctx->g;
+    cudaStream_t s = ctx->stream;
+    const int sms = ctx->num_sms;
+    Plan& p = ctx->plan;
+    p.split_len = split_len;
+    p.task_nnz = task_nnz;
+    CL_TRY(dalloc(ctx, &p.counter, 1));
+    if (g.n == 0) {
+        p.valid = true;
+        return CLEORA_OK;
+    }
+    uint8_t* brk = nullptr;
+    int32_t* rows = nullptr;
+    int64_t* scal = nullptr;
+    int64_t* work = nullptr;  // 6 arrays of nb int64
+    int rc = CLEORA_OK;
+    int64_t nb = 0;
+    auto cleanup = [&]() {
+        dfree(ctx, brk);
+        dfree(ctx, rows);
+        dfree(ctx, scal);
+        dfree(ctx, work);
+    };
+    do {
+        if ((rc = dalloc(ctx, &brk, (size_t)g.n))) break;
+        if ((rc = dalloc(ctx, &rows, (size_t)g.n))) break;
+        if ((rc = dalloc(ctx, &scal, 4))) break;
+        k_plan_mark<<<grid_for(g.n, 256, sms), 256, 0, s>>>(g.rowptr, g.n, split_len, task_nnz, brk);
+        ctx->launches++;
+        size_t tb = 0;
+        thrust::counting_iterator<int32_t> it(0);
+        cudaError_t e = cub::DeviceSelect::Flagged(nullptr, tb, it, brk, rows, scal, g.n, s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "select", __FILE__, __LINE__); break; }
+        void* tmp = nullptr;
+        if ((rc = dalloc_bytes(ctx, &tmp, tb))) break;
+        e = cub::DeviceSelect::Flagged(tmp, tb, it, brk, rows, scal, g.n, s);
+        dfree(ctx, tmp);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "select", __FILE__, __LINE__); break; }
+        e = cudaMemcpyAsync(&nb, scal, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "plan count", __FILE__, __LINE__); break; }
+        if ((rc = dalloc(ctx, &work, (size_t)(6 * nb)))) break;
+        int64_t *chunks = work, *normal = work + nb, *split = work + 2 * nb;
+        int64_t *cbase = work + 3 * nb, *nbase = work + 4 * nb, *sbase = work + 5 * nb;
+        k_plan_counts<<<grid_for(nb, 256, sms), 256, 0, s>>>(g.rowptr, rows, nb, split_len, chunks,
+                                                             normal, split);
+        ctx->launches++;
+        tb = 0;
+        e = cub::DeviceScan::ExclusiveSum(nullptr, tb, chunks, cbase, nb, s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
+        if ((rc = dalloc_bytes(ctx, &tmp, tb))) break;
+        e = cub::DeviceScan::ExclusiveSum(tmp, tb, chunks, cbase, nb, s);
+        if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tmp, tb, normal, nbase, nb, s);
+        if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tmp, tb, split, sbase, nb, s);
+        dfree(ctx, tmp);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
+        int64_t last[6];
+        const int64_t* srcs[6] = {cbase + nb - 1, chunks + nb - 1, nbase + nb - 1,
+                                  normal + nb - 1, sbase + nb - 1, split + nb - 1};
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(&last[k], srcs[k], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "plan totals", __FILE__, __LINE__); break; }
+        p.nsplit_chunks = last[0] + last[1];
+        const int64_t total_normal = last[2] + last[3];
+        p.nsplit_rows = last[4] + last[5];
+        p.ntasks = p.nsplit_chunks + total_normal;
+        if ((rc = dalloc(ctx, &p.tasks, (size_t)p.ntasks))) break;
+        if ((rc = dalloc(ctx, &p.split_base, (size_t)(p.nsplit_rows ? p.nsplit_rows : 1)))) break;
+        if ((rc = dalloc(ctx, &p.split_count, (size_t)(p.nsplit_rows ? p.nsplit_rows : 1)))) break;
+        e = cudaMemsetAsync(p.split_count, 0, sizeof(int32_t) * (p.nsplit_rows ? p.nsplit_rows : 1), s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "memset", __FILE__, __LINE__); break; }
+        k_plan_fill<<<grid_for(nb, 256, sms), 256, 0, s>>>(rows, nb, g.n, chunks, cbase, nbase, sbase,
+                                                           p.nsplit_chunks, p.tasks, p.split_base);
+        ctx->launches++;
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "plan fill", __FILE__, __LINE__); break; }
+    } while (0);
+    cleanup();
+    if (rc == CLEORA_OK) p.valid = true;
+    return rc;
+}
+
+int plan_ensure(cleora_ctx* ctx) {
+    int64_t split_len = ctx->opt[CLEORA_OPT_SPLIT_LEN] > 0 ? ctx->opt[CLEORA_OPT_SPLIT_LEN] : DEFAULT_SPLIT_LEN;
+    int64_t task_nnz = ctx->opt[CLEORA_OPT_TASK_NNZ] > 0 ? ctx->opt[CLEORA_OPT_TASK_NNZ] : DEFAULT_TASK_NNZ;
+    Plan& p = ctx->plan;
+    if (!p.valid || p.split_len != split_len || p.task_nnz != task_nnz)
+        CL_TRY(plan_build(ctx, split_len, task_nnz));
+    if (ctx->d > 0 && p.nsplit_chunks > 0 && p.partials_d != ctx->d) {
+        dfree_null(ctx, p.partials);
+        CL_TRY(dalloc(ctx, &p.partials, (size_t)(p.nsplit_chunks * ctx->d)));
+        p.partials_d = ctx->d;
+    }
+    return CLEORA_OK;
+}
+
+int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
+    const Graph& g = ctx->g;
+    const Plan& p = ctx->plan;
+    if (g.n == 0 || p.ntasks == 0) return CLEORA_OK;
+    const Shape sh = choose_shape(ctx, ctx->d, ctx->dtype);
+    prop::Args a;
+    a.rowptr = g.rowptr;
+    a.col = g.col;
+    a.val = g.val;
+    a.Tin = static_cast<const unsigned char*>(Tin);
+    a.Tout = static_cast<unsigned char*>(Tout);
+    a.n = g.n;
+    a.nnz = g.nnz;
+    a.row_bytes = (int64_t)ctx->d * (ctx->dtype == CLEORA_F32 ? 4 : 2);
+    a.chunks = sh.chunks;
+    a.d = ctx->d;
+    a.split_len = p.split_len;
+    a.tasks = p.tasks;
+    a.ntasks = p.ntasks;
+    a.counter = p.counter;
+    a.split_base = p.split_base;
+    a.split_count = p.split_count;
+    a.partials = p.partials;
+    a.err = ctx->err_flag;
+    CL_CUDA(ctx, cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), ctx->stream));
+    const int bps = (int)ctx->opt[CLEORA_OPT_BLOCKS_PER_SM];
+    cudaError_t e;
+    int grid = 0;
+    if (ctx->dtype == CLEORA_F32)
+        e = sh.vec == 16 ? prop::launch_f32_v16(sh, a, g.has_val, bps, ctx->num_sms, ctx->stream, &grid)
+                         : prop::launch_f32_v8(sh, a, g.has_val, bps, ctx->num_sms, ctx->stream, &grid);
+    else
+        e = sh.vec == 16 ? prop::launch_bf16_v16(sh, a, g.has_val, bps, ctx->num_sms, ctx->stream, &grid)
+                         : prop::launch_bf16_v8(sh, a, g.has_val, bps, ctx->num_sms, ctx->stream, &grid);
+    ctx->launches++;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "propagate launch", __FILE__, __LINE__);
+    return CLEORA_OK;
+}
+
+}  // namespace cleora

@@ -1,0 +1,460 @@
+// Fused propagate kernel: one Cleora iteration T_k = rownorm_L2(M T_{k-1})
+// (arXiv 2102.02302, Algorithm 1: multiply by M, then L2-normalise rows).
+//
+// Design (sm_103a):
+//  * Persistent grid; each warp pulls tasks from a global counter.  A task is either a run
+//    of consecutive rows holding about `task_nnz` entries, or one chunk of a long row.
+//  * A row of T is covered by G lanes, each holding CPL vectors of VEC bytes (16 B or 8 B
+//    gathers, coalesced across the G lanes).  The warp has P = 32/G lane groups:
+//      mode 1: the groups split one row's entries and add their sums by xor-shuffles;
+//      mode 2: each group owns its own rows (more rows in flight for short rows).
+//  * Column indices (and values) are read once as a coalesced 32-entry window per warp and
+//    broadcast by shuffles; rows keep reusing the window until they leave it.
+//  * Accumulation and the row norm are FP32 for both storage types; the norm's reduction is
+//    a fixed shuffle butterfly and the output is written once (streaming store).
+//  * Long rows are split into chunks; each chunk's FP32 partial sum goes to a slot, and the
+//    warp that finishes a row's last chunk adds the slots in a fixed order, normalises and
+//    writes the row.  No floating-point atomics, so results are deterministic.
+//  * Unit-weight graphs need no per-entry value: M_ab = 1/deg_a is the same for the whole
+//    row, and the L2 normalisation removes that common factor exactly, so the kernel sums
+//    neighbour rows and normalises.
+#pragma once
+
+#include "common.cuh"
+
+namespace cleora {
+namespace prop {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Args {
+    const int64_t* rowptr;
+    const int32_t* col;
+    const float* val;
+    const unsigned char* Tin;
+    unsigned char* Tout;
+    int64_t n;
+    int64_t nnz;
+    int64_t row_bytes;
+    int chunks;      // vectors per row
+    int d;
+    int64_t split_len;
+    const Task* tasks;
+    int64_t ntasks;
+    unsigned long long* counter;
+    const int64_t* split_base;
+    int32_t* split_count;
+    float* partials;
+    int* err;
+};
+
+template <int VEC> struct VecT;
+template <> struct VecT<16> { using T = uint4; };
+template <> struct VecT<8> { using T = uint2; };
+
+__device__ __forceinline__ uint4 ld_gather(const uint4* p) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_gather(const uint2* p) {
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void st_stream(uint4* p, uint4 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(uint2* p, uint2 v) { __stcs(p, v); }
+
+__device__ __forceinline__ uint32_t word(const uint4& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ uint32_t word(const uint2& v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ void set_word(uint4& v, int i, uint32_t w) {
+    if (i == 0) v.x = w; else if (i == 1) v.y = w; else if (i == 2) v.z = w; else v.w = w;
+}
+__device__ __forceinline__ void set_word(uint2& v, int i, uint32_t w) {
+    if (i == 0) v.x = w; else v.y = w;
+}
+
+// Element traits: FP32 has one element per 32-bit word, BF16 two.
+template <typename ST> struct EL;
+template <> struct EL<float> {
+    static constexpr int PER_WORD = 1;
+    __device__ static __forceinline__ void unpack(uint32_t w, float* f) { f[0] = __uint_as_float(w); }
+    __device__ static __forceinline__ uint32_t pack(const float* f) { return __float_as_uint(f[0]); }
+};
+template <> struct EL<__nv_bfloat16> {
+    static constexpr int PER_WORD = 2;
+    __device__ static __forceinline__ void unpack(uint32_t w, float* f) {
+        f[0] = __uint_as_float(w << 16);
+        f[1] = __uint_as_float(w & 0xffff0000u);
+    }
+    __device__ static __forceinline__ uint32_t pack(const float* f) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(f[0], f[1]);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+};
+
+template <typename ST, int VEC, int CPL, int G, bool HV>
+struct Kern {
+    using VT = typename VecT<VEC>::T;
+    static constexpr int W = VEC / 4;                       // 32-bit words per vector
+    static constexpr int EPV = W * EL<ST>::PER_WORD;        // elements per vector
+    static constexpr int P = 32 / G;                        // lane groups per warp
+    static constexpr int U = CPL >= 8 ? 1 : 8 / CPL;        // entries in flight per group
+
+    struct Acc {
+        float v[CPL][EPV];
+        __device__ __forceinline__ void zero() {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) v[i][e] = 0.f;
+        }
+    };
+
+    __device__ static __forceinline__ void add_vec(Acc& acc, int i, const VT& x, float w) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            float f[EL<ST>::PER_WORD];
+            EL<ST>::unpack(word(x, k), f);
+#pragma unroll
+            for (int h = 0; h < EL<ST>::PER_WORD; ++h) {
+                if (HV) acc.v[i][k * EL<ST>::PER_WORD + h] = fmaf(w, f[h], acc.v[i][k * EL<ST>::PER_WORD + h]);
+                else acc.v[i][k * EL<ST>::PER_WORD + h] += f[h];
+            }
+        }
+    }
+
+    __device__ static __forceinline__ VT zero_vec() {
+        VT z;
+#pragma unroll
+        for (int k = 0; k < W; ++k) set_word(z, k, 0u);
+        return z;
+    }
+
+    // Entries j = j0 + u*P + g (u < U) of a window of column indices held one per lane
+    // (`mc`, `mw`), restricted to j < jh; all 32 lanes execute the shuffles.
+    __device__ static __forceinline__ void gather_batch(const Args& a, Acc& acc, int mc, float mw,
+                                                        int j0, int jh, int g, int lg) {
+        VT x[U][CPL];
+        float w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * P + g;
+            const int c = __shfl_sync(FULL, mc, j & 31);
+            const float wu = HV ? __shfl_sync(FULL, mw, j & 31) : 1.f;
+            bool ok = j < jh;
+            if (ok && (unsigned)c >= (unsigned)a.n) {  // corrupt index: flag, skip
+                atomicOr(a.err, 1);
+                ok = false;
+            }
+            w[u] = ok ? wu : 0.f;
+            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)(ok ? c : 0) * a.row_bytes);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int q = i * G + lg;
+                x[u][i] = (ok && q < a.chunks) ? ld_gather(rp + q) : zero_vec();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) add_vec(acc, i, x[u][i], w[u]);
+    }
+
+    // Same for one lane group working alone (mode 2): window of G entries, entries j0+u.
+    __device__ static __forceinline__ void gather_batch_group(const Args& a, Acc& acc, int mc, float mw,
+                                                              int j0, int jh, int lg, unsigned gmask) {
+        VT x[U][CPL];
+        float w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u;
+            const int c = __shfl_sync(gmask, mc, j & (G - 1), G);
+            const float wu = HV ? __shfl_sync(gmask, mw, j & (G - 1), G) : 1.f;
+            bool ok = j < jh;
+            if (ok && (unsigned)c >= (unsigned)a.n) {
+                atomicOr(a.err, 1);
+                ok = false;
+            }
+            w[u] = ok ? wu : 0.f;
+            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)(ok ? c : 0) * a.row_bytes);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int q = i * G + lg;
+                x[u][i] = (ok && q < a.chunks) ? ld_gather(rp + q) : zero_vec();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) add_vec(acc, i, x[u][i], w[u]);
+    }
+
+    // Own previous row (a row without entries keeps it, renormalised).
+    __device__ static __forceinline__ void load_own(const Args& a, Acc& acc, int64_t r, int lg) {
+        const VT* rp = reinterpret_cast<const VT*>(a.Tin + r * a.row_bytes);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int q = i * G + lg;
+            if (q < a.chunks) {
+                VT x = ld_gather(rp + q);
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    float f[EL<ST>::PER_WORD];
+                    EL<ST>::unpack(word(x, k), f);
+#pragma unroll
+                    for (int h = 0; h < EL<ST>::PER_WORD; ++h) acc.v[i][k * EL<ST>::PER_WORD + h] = f[h];
+                }
+            }
+        }
+    }
+
+    // Sum the P groups' partial sums (fixed butterfly: every group ends with the same bits).
+    __device__ static __forceinline__ void reduce_groups(Acc& acc) {
+#pragma unroll
+        for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) acc.v[i][e] += __shfl_xor_sync(FULL, acc.v[i][e], off);
+    }
+
+    // L2-normalise within a lane group and store the row (group 0 stores in mode 1).
+    __device__ static __forceinline__ void finish_row(const Args& a, Acc& acc, int64_t r, int lg,
+                                                      bool store, unsigned gmask) {
+        float ss = 0.f;
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            if (i * G + lg < a.chunks) {
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) ss = fmaf(acc.v[i][e], acc.v[i][e], ss);
+            }
+        }
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) ss += __shfl_xor_sync(gmask, ss, off);
+        const float inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+        if (!store) return;
+        VT* op = reinterpret_cast<VT*>(a.Tout + r * a.row_bytes);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int q = i * G + lg;
+            if (q < a.chunks) {
+                VT x;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    float f[EL<ST>::PER_WORD];
+#pragma unroll
+                    for (int h = 0; h < EL<ST>::PER_WORD; ++h) f[h] = acc.v[i][k * EL<ST>::PER_WORD + h] * inv;
+                    set_word(x, k, EL<ST>::pack(f));
+                }
+                st_stream(op + q, x);
+            }
+        }
+    }
+
+    // Accumulate entries [k0, k1) with the whole warp (groups interleave entries).
+    __device__ static __forceinline__ void range_coop(const Args& a, Acc& acc, int64_t k0, int64_t k1,
+                                                      int lane, int g, int lg) {
+        for (int64_t cb = k0; cb < k1; cb += 32) {
+            const int jh = (int)min((int64_t)32, k1 - cb);
+            int mc = 0;
+            float mw = 0.f;
+            if (lane < jh) {
+                mc = __ldcs(a.col + cb + lane);
+                if (HV) mw = __ldcs(a.val + cb + lane);
+            }
+            for (int j0 = 0; j0 < jh; j0 += P * U) gather_batch(a, acc, mc, mw, j0, jh, g, lg);
+        }
+    }
+
+    // Mode 1: the warp walks rows [rb, re) one at a time; rowptr and column windows are
+    // loaded 32 at a time and reused across consecutive rows.
+    __device__ static void rows_coop(const Args& a, int64_t rb, int64_t re, int lane, int g, int lg) {
+        int64_t wr = rb, lo = 0, hi = 0;
+        if (wr + lane < re) {
+            lo = a.rowptr[wr + lane];
+            hi = a.rowptr[wr + lane + 1];
+        }
+        int64_t cb = -64;  // column window [cb, cb + 32)
+        int mc = 0;
+        float mw = 0.f;
+        for (int64_t r = rb; r < re; ++r) {
+            if (r - wr == 32) {
+                wr = r;
+                lo = hi = 0;
+                if (wr + lane < re) {
+                    lo = a.rowptr[wr + lane];
+                    hi = a.rowptr[wr + lane + 1];
+                }
+            }
+            const int64_t beg = __shfl_sync(FULL, lo, (int)(r - wr));
+            const int64_t end = __shfl_sync(FULL, hi, (int)(r - wr));
+            Acc acc;
+            acc.zero();
+            if (beg == end) {
+                if (g == 0) load_own(a, acc, r, lg);
+            }
+            for (int64_t k = beg; k < end;) {
+                if (k < cb || k >= cb + 32) {
+                    cb = k;
+                    mc = 0;
+                    mw = 0.f;
+                    if (cb + lane < a.nnz) {
+                        mc = __ldcs(a.col + cb + lane);
+                        if (HV) mw = __ldcs(a.val + cb + lane);
+                    }
+                }
+                const int jl = (int)(k - cb);
+                const int jh = (int)min((int64_t)32, end - cb);
+                for (int j0 = jl; j0 < jh; j0 += P * U) gather_batch(a, acc, mc, mw, j0, jh, g, lg);
+                k = cb + jh;
+            }
+            reduce_groups(acc);
+            finish_row(a, acc, r, lg, g == 0, FULL);
+        }
+    }
+
+    // Mode 2: lane group g owns rows rb + g, rb + g + P, ...
+    __device__ static void rows_group(const Args& a, int64_t rb, int64_t re, int g, int lg) {
+        const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (g * G));
+        for (int64_t r = rb + g; r < re; r += P) {
+            const int64_t beg = a.rowptr[r], end = a.rowptr[r + 1];
+            Acc acc;
+            acc.zero();
+            if (beg == end) load_own(a, acc, r, lg);
+            for (int64_t cb = beg; cb < end; cb += G) {
+                const int jh = (int)min((int64_t)G, end - cb);
+                int mc = 0;
+                float mw = 0.f;
+                if (lg < jh) {
+                    mc = __ldcs(a.col + cb + lg);
+                    if (HV) mw = __ldcs(a.val + cb + lg);
+                }
+                for (int j0 = 0; j0 < jh; j0 += U) gather_batch_group(a, acc, mc, mw, j0, jh, lg, gmask);
+            }
+            finish_row(a, acc, r, lg, true, gmask);
+        }
+    }
+
+    // One chunk of a split row; the last chunk to finish combines all partial slots.
+    __device__ static void split_chunk(const Args& a, const Task& t, int lane, int g, int lg) {
+        const int64_t r = t.a;
+        const int64_t beg = a.rowptr[r], end = a.rowptr[r + 1];
+        const int64_t k0 = beg + (int64_t)t.c * a.split_len;
+        const int64_t k1 = min(end, k0 + a.split_len);
+        Acc acc;
+        acc.zero();
+        range_coop(a, acc, k0, k1, lane, g, lg);
+        reduce_groups(acc);
+        const int64_t base = a.split_base[t.b];
+        float* slot = a.partials + (base + t.c) * (int64_t)a.d;
+        if (g == 0) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int q = i * G + lg;
+                if (q < a.chunks) {
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e) __stcg(slot + q * EPV + e, acc.v[i][e]);
+                }
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        int prev = 0;
+        if (lane == 0) prev = atomicAdd(a.split_count + t.b, 1);
+        prev = __shfl_sync(FULL, prev, 0);
+        if (prev != t.k - 1) return;
+        // Last arrival: add slots 0..k-1 (group g takes c = g, g+P, ...), then the butterfly.
+        __threadfence();
+        acc.zero();
+        for (int c = g; c < t.k; c += P) {
+            const float* s = a.partials + (base + c) * (int64_t)a.d;
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int q = i * G + lg;
+                if (q < a.chunks) {
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e) acc.v[i][e] += __ldcg(s + q * EPV + e);
+                }
+            }
+        }
+        reduce_groups(acc);
+        finish_row(a, acc, r, lg, g == 0, FULL);
+        if (lane == 0) a.split_count[t.b] = 0;  // ready for the next launch
+    }
+};
+
+template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
+__global__ void __launch_bounds__(256) k_propagate(Args a) {
+    using K = Kern<ST, VEC, CPL, G, HV>;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G, lg = lane % G;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= (unsigned long long)a.ntasks) break;
+        const Task task = a.tasks[t];
+        if (task.c >= 0) {
+            K::split_chunk(a, task, lane, g, lg);
+        } else if (MODE == 1 || G == 32) {
+            K::rows_coop(a, task.a, task.b, lane, g, lg);
+        } else {
+            K::rows_group(a, task.a, task.b, g, lg);
+        }
+        __syncwarp();
+    }
+}
+
+// Host-side launcher for one storage type, vector width and value mode.
+template <typename ST, int VEC, bool HV>
+struct Launch {
+    template <int CPL, int G, int MODE>
+    static cudaError_t go(const Args& a, int blocks_per_sm, int num_sms, cudaStream_t s, int* grid_out) {
+        auto kern = k_propagate<ST, VEC, CPL, G, MODE, HV>;
+        int bps = blocks_per_sm;
+        if (bps <= 0) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0);
+            if (e != cudaSuccess) return e;
+            if (bps < 1) bps = 1;
+        }
+        int grid = bps * num_sms;
+        if (grid_out) *grid_out = grid;
+        kern<<<grid, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t run(const Shape& sh, const Args& a, int bps, int sms, cudaStream_t s, int* grid) {
+        const int m = sh.mode;
+        if (sh.cpl == 1) {
+            switch (sh.G) {
+                case 1:  return m == 2 ? go<1, 1, 2>(a, bps, sms, s, grid) : go<1, 1, 1>(a, bps, sms, s, grid);
+                case 2:  return m == 2 ? go<1, 2, 2>(a, bps, sms, s, grid) : go<1, 2, 1>(a, bps, sms, s, grid);
+                case 4:  return m == 2 ? go<1, 4, 2>(a, bps, sms, s, grid) : go<1, 4, 1>(a, bps, sms, s, grid);
+                case 8:  return m == 2 ? go<1, 8, 2>(a, bps, sms, s, grid) : go<1, 8, 1>(a, bps, sms, s, grid);
+                case 16: return m == 2 ? go<1, 16, 2>(a, bps, sms, s, grid) : go<1, 16, 1>(a, bps, sms, s, grid);
+                case 32: return go<1, 32, 1>(a, bps, sms, s, grid);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+        if (sh.G != 32) return cudaErrorInvalidValue;
+        switch (sh.cpl) {
+            case 2: return go<2, 32, 1>(a, bps, sms, s, grid);
+            case 4: return go<4, 32, 1>(a, bps, sms, s, grid);
+            case 8: return go<8, 32, 1>(a, bps, sms, s, grid);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+};
+
+// Entry points defined in the per-type translation units.
+cudaError_t launch_f32_v16(const Shape&, const Args&, bool hv, int bps, int sms, cudaStream_t, int*);
+cudaError_t launch_f32_v8(const Shape&, const Args&, bool hv, int bps, int sms, cudaStream_t, int*);
+cudaError_t launch_bf16_v16(const Shape&, const Args&, bool hv, int bps, int sms, cudaStream_t, int*);
+cudaError_t launch_bf16_v8(const Shape&, const Args&, bool hv, int bps, int sms, cudaStream_t, int*);
+
+}  // namespace prop
+}  // namespace cleora

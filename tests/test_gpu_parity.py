@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Integer work (ids, CSR, degrees, stored FP32 values, T_0 bits) must match bit for bit.
+FP32 storage: max |err| <= 1e-5 per entry against FP64.  BF16 storage: max |err| <= 2e-2
+and per-row cosine >= 0.999.  Cases span several tasks, split rows and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+BF16_TOL = 2e-2
+BF16_COS = 0.999
+
+
+def _ctx():
+    import paper_2102_02302_gb300 as pkg
+    return pkg.Context(0)
+
+
+def gpu_run(edges, d, iters, seed=0, storage="f32", opts=None):
+    with _ctx() as ctx:
+        for k, v in (opts or {}).items():
+            ctx.set_option(k, v)
+        ctx.graph_build(edges.src, edges.dst, edges.weights, edges.directed)
+        n = ctx.info()["n"]
+        ctx.init(d, seed, storage)
+        out = np.empty((n, d), np.float32)
+        ctx.propagate(iters, out)
+        ctx.sync()
+        return ctx.node_ids(), out
+
+
+def bf16_bits(x):
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return (((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
+
+
+def bf16_value(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+def assert_close_f32(got, want):
+    err = np.abs(got.astype(np.float64) - want)
+    assert err.max() <= F32_TOL, f"max |err| {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+
+
+def assert_close_bf16(got, want):
+    err = np.abs(got.astype(np.float64) - want)
+    assert err.max() <= BF16_TOL, f"max |err| {err.max():.3e}"
+    g = got.astype(np.float64)
+    cos = (g * want).sum(1) / (np.linalg.norm(g, axis=1) * np.linalg.norm(want, axis=1) + 1e-300)
+    nz = np.linalg.norm(want, axis=1) > 0
+    assert cos[nz].min() >= BF16_COS, f"min cosine {cos[nz].min():.6f}"
+
+
+GRAPHS = {
+    "undirected_unit": lambda: synth.random_multigraph(300, 1500, 1, False, False, self_loops=False),
+    "undirected_dups_loops": lambda: synth.random_multigraph(200, 2000, 2, False, False),
+    "directed_weighted_sinks": lambda: synth.random_multigraph(500, 900, 3, True, True),
+    "directed_unit_dups": lambda: synth.random_multigraph(257, 3000, 4, True, False),
+    "power_law_small": lambda: synth.SMALL.generate(),
+    "star_hub": lambda: synth.star(5000, seed=5),
+}
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return {k: f() for k, f in GRAPHS.items()}
+
+
+@pytest.fixture(scope="module")
+def oracle_graphs(graphs):
+    return {k: oracle.build_from(e) for k, e in graphs.items()}
+
+
+# --------------------------------------------------------------------------------------
+# Integer work: bit-exact
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_csr_is_bit_exact(name, graphs, oracle_graphs):
+    e, g = graphs[name], oracle_graphs[name]
+    with _ctx() as ctx:
+        ctx.graph_build(e.src, e.dst, e.weights, e.directed)
+        c = ctx.csr()
+        ids = ctx.node_ids()
+    assert np.array_equal(ids, g.ids)
+    assert c["n"] == g.n and c["nnz"] == g.nnz
+    assert c["has_val"] == g.has_val
+    assert np.array_equal(c["rowptr"], g.rowptr)
+    assert np.array_equal(c["col"], g.col)
+    assert np.array_equal(c["deg"].view(np.uint64), g.deg.view(np.uint64))
+    assert np.array_equal(c["inv_deg"].view(np.uint32), g.inv_deg32.view(np.uint32))
+    if g.has_val:
+        want = g.val32
+    else:
+        want = np.repeat(g.inv_deg32, np.diff(g.rowptr))
+    assert np.array_equal(c["val"].view(np.uint32), want.view(np.uint32))
+    assert c["max_row_len"] == int(np.diff(g.rowptr).max())
+
+
+@pytest.mark.parametrize("d", [8, 24, 128, 1024])
+def test_init_bits(d, graphs, oracle_graphs):
+    e, g = graphs["directed_weighted_sinks"], oracle_graphs["directed_weighted_sinks"]
+    want = oracle.init(g.ids, d, seed=12345)
+    with _ctx() as ctx:
+        ctx.graph_build(e.src, e.dst, e.weights, e.directed)
+        ctx.init(d, 12345, "f32")
+        got = ctx.embeddings("f32")
+        assert np.array_equal(got, want.astype(np.float32))
+        assert np.array_equal(got.astype(np.float64), want)  # exact in FP32
+        ctx.init(d, 12345, "bf16")
+        bits = ctx.embeddings("bf16")
+        assert np.array_equal(bits, bf16_bits(want.astype(np.float32)))
+
+
+# --------------------------------------------------------------------------------------
+# Propagation: FP32 and BF16 tolerances
+# --------------------------------------------------------------------------------------
+
+SCHEDULES = {
+    "default": {},
+    "split_rows": {"split_len": 256, "task_nnz": 64},
+    "vec8": {"vec_bytes": 8},
+    "row_groups": {"row_mode": 2},
+    "row_groups_vec8_split": {"row_mode": 2, "vec_bytes": 8, "split_len": 300, "task_nnz": 100},
+    "one_block": {"blocks_per_sm": 1, "task_nnz": 1024},
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("d", [16, 128])
+def test_f32_matches_oracle(name, d, graphs, oracle_graphs):
+    e, g = graphs[name], oracle_graphs[name]
+    T0 = oracle.init(g.ids, d, 7)
+    for iters in (1, 4):
+        want = oracle.propagate(g, T0, iters)
+        ids, got = gpu_run(e, d, iters, seed=7)
+        assert np.array_equal(ids, g.ids)
+        assert_close_f32(got, want)
+
+
+@pytest.mark.parametrize("sched", list(SCHEDULES))
+@pytest.mark.parametrize("d", [8, 64, 96, 256, 1024])
+def test_f32_schedules_and_dims(sched, d, graphs, oracle_graphs):
+    name = "power_law_small" if d <= 256 else "undirected_dups_loops"
+    e, g = graphs[name], oracle_graphs[name]
+    want = oracle.propagate(g, oracle.init(g.ids, d, 3), 3)
+    _, got = gpu_run(e, d, 3, seed=3, opts=SCHEDULES[sched])
+    assert_close_f32(got, want)
+
+
+@pytest.mark.parametrize("sched", list(SCHEDULES))
+@pytest.mark.parametrize("name", ["power_law_small", "directed_weighted_sinks", "star_hub"])
+@pytest.mark.parametrize("d", [64, 128, 256])
+def test_bf16_matches_oracle(sched, name, d, graphs, oracle_graphs):
+    e, g = graphs[name], oracle_graphs[name]
+    # BF16 storage starts from the rounded T_0, which the oracle takes as its input
+    T0 = bf16_value(bf16_bits(oracle.init(g.ids, d, 9).astype(np.float32))).astype(np.float64)
+    want = oracle.propagate(g, T0, 4)
+    _, got = gpu_run(e, d, 4, seed=9, storage="bf16", opts=SCHEDULES[sched])
+    assert_close_bf16(got, want)
+
+
+def test_rows_have_unit_norm_and_sinks_keep_their_row(graphs, oracle_graphs):
+    e, g = graphs["directed_weighted_sinks"], oracle_graphs["directed_weighted_sinks"]
+    _, got = gpu_run(e, 32, 1, seed=1)
+    np.testing.assert_allclose(np.linalg.norm(got.astype(np.float64), axis=1), 1.0, atol=2e-6)
+    sinks = np.where(np.diff(g.rowptr) == 0)[0]
+    assert sinks.size > 10
+    T0 = oracle.init(g.ids, 32, 1)
+    want = T0[sinks] / np.linalg.norm(T0[sinks], axis=1, keepdims=True)
+    assert_close_f32(got[sinks], want)
+
+
+# --------------------------------------------------------------------------------------
+# Determinism, resume, edge order
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_deterministic_and_resumable(storage, graphs):
+    e = graphs["power_law_small"]
+    opts = {"split_len": 256, "task_nnz": 128}
+    _, a = gpu_run(e, 64, 4, storage=storage, opts=opts)
+    _, b = gpu_run(e, 64, 4, storage=storage, opts=opts)
+    assert np.array_equal(a, b)
+    with _ctx() as ctx:
+        for k, v in opts.items():
+            ctx.set_option(k, v)
+        ctx.graph_build(e.src, e.dst, None, False)
+        ctx.init(64, 0, storage)
+        ctx.propagate(2)
+        ckpt = ctx.embeddings(storage)
+        out = np.empty_like(a)
+        ctx.propagate(2, out)
+        assert np.array_equal(out, a)
+        # resume from the checkpoint
+        ctx.set_embeddings(ckpt, storage, iteration=2)
+        ctx.propagate(2, out)
+        assert np.array_equal(out, a)
+
+
+def test_edge_order_gives_identical_csr_and_embeddings(graphs):
+    e = graphs["undirected_dups_loops"]
+    perm = np.random.default_rng(0).permutation(e.num_edges)
+    flip = np.random.default_rng(1).random(e.num_edges) < 0.5
+    e2 = synth.EdgeList(np.where(flip, e.dst, e.src)[perm].copy(),
+                        np.where(flip, e.src, e.dst)[perm].copy(), None, False)
+    _, a = gpu_run(e, 128, 3)
+    _, b = gpu_run(e2, 128, 3)
+    assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------------------
+# Edge cases and errors
+# --------------------------------------------------------------------------------------
+
+def test_empty_graph_and_tiny_graphs():
+    import paper_2102_02302_gb300 as pkg
+    with _ctx() as ctx:
+        ctx.graph_build(np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+        assert ctx.info()["n"] == 0
+        ctx.init(16, 0)
+        ctx.propagate(3, np.empty((0, 16), np.float32))
+    one = synth.from_index_pairs([0], [1], False)
+    g = oracle.build_from(one)
+    _, got = gpu_run(one, 8, 2)
+    assert_close_f32(got, oracle.propagate(g, oracle.init(g.ids, 8, 0), 2))
+    loop = synth.from_index_pairs([0], [0], True)
+    g = oracle.build_from(loop)
+    _, got = gpu_run(loop, 8, 5)
+    assert_close_f32(got, oracle.propagate(g, oracle.init(g.ids, 8, 0), 5))
+    # a row whose neighbours cancel exactly: y = T[a] + (-T[a]) is impossible to build from
+    # one graph, so the zero-norm guard is covered by zero embeddings set explicitly
+    with _ctx() as ctx:
+        ctx.graph_build(one.src, one.dst, None, False)
+        ctx.init(8, 0)
+        ctx.set_embeddings(np.zeros((2, 8), np.float32))
+        out = np.ones((2, 8), np.float32)
+        ctx.propagate(1, out)
+        assert np.all(out == 0)
+    assert pkg  # imported for the error types below
+
+
+def test_errors_are_reported_not_crashed():
+    import paper_2102_02302_gb300 as pkg
+    e = synth.from_index_pairs([0, 1], [1, 2], True, weights=[1.0, 0.0])
+    with _ctx() as ctx:
+        with pytest.raises(pkg.CleoraError) as ex:
+            ctx.graph_build(e.src, e.dst, e.weights, True)
+        assert ex.value.status == pkg.CLEORA_ERR_INVALID_ARG
+        with pytest.raises(pkg.CleoraError) as ex:
+            ctx.init(16, 0)
+        assert ex.value.status == pkg.CLEORA_ERR_STATE
+        ctx.graph_build(e.src, e.dst, None, True)
+        with pytest.raises(pkg.CleoraError) as ex:
+            ctx.propagate(1)
+        assert ex.value.status == pkg.CLEORA_ERR_STATE
+        for bad_d in (0, 12, 2048):
+            with pytest.raises(pkg.CleoraError):
+                ctx.init(bad_d, 0)
+        with pytest.raises(pkg.CleoraError):
+            ctx.set_option("vec_bytes", 4)
+        ctx.init(16, 0)
+        ctx.propagate(1)
+        ctx.sync()
+
+
+def test_device_resident_inputs_and_outputs(graphs, oracle_graphs):
+    import torch
+    e, g = graphs["directed_weighted_sinks"], oracle_graphs["directed_weighted_sinks"]
+    src = torch.from_numpy(e.src.view(np.int64)).cuda()
+    dst = torch.from_numpy(e.dst.view(np.int64)).cuda()
+    w = torch.from_numpy(e.weights).cuda()
+    torch.cuda.synchronize()  # the context works on its own stream
+    with _ctx() as ctx:
+        ctx.graph_build(src, dst, w, True)
+        ctx.init(128, 5)
+        out = torch.empty((g.n, 128), dtype=torch.float32, device="cuda")
+        ctx.propagate(4, out)
+        ctx.sync()
+        got = out.cpu().numpy()
+    assert_close_f32(got, oracle.propagate(g, oracle.init(g.ids, 128, 5), 4))
