@@ -304,7 +304,10 @@ def main():
     edges = make_edges(spec, torch.device("cuda", device))
     gen_s = time.perf_counter() - t
 
-    stream = torch.cuda.current_stream()
+    # A dedicated stream: the library and the CUDA events must share it (torch's default
+    # stream has handle 0, which the C ABI reads as "create a private stream").
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
     storages = ["bf16", "f32"] if args.storage == "both" else [args.storage]
     results = {}
     with pkg.Context(device, stream.cuda_stream) as ctx:

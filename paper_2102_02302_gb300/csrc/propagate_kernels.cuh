@@ -104,13 +104,26 @@ struct Kern {
     static constexpr int P = 32 / G;                        // lane groups per warp
     static constexpr int U = CPL >= 8 ? 1 : 8 / CPL;        // entries in flight per group
 
+    // Two-level sum: `v` collects at most one 32-entry window, then is added into `t`.  Every
+    // serial FP32 chain stays short (window + windows-per-row) even for a row of thousands of
+    // nearly equal neighbour rows, where one long chain would build a systematic error.
     struct Acc {
         float v[CPL][EPV];
+        float t[CPL][EPV];
         __device__ __forceinline__ void zero() {
 #pragma unroll
             for (int i = 0; i < CPL; ++i)
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) v[i][e] = 0.f;
+                for (int e = 0; e < EPV; ++e) v[i][e] = t[i][e] = 0.f;
+        }
+        __device__ __forceinline__ void flush() {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) {
+                    t[i][e] += v[i][e];
+                    v[i][e] = 0.f;
+                }
         }
     };
 
@@ -206,7 +219,7 @@ struct Kern {
                     float f[EL<ST>::PER_WORD];
                     EL<ST>::unpack(word(x, k), f);
 #pragma unroll
-                    for (int h = 0; h < EL<ST>::PER_WORD; ++h) acc.v[i][k * EL<ST>::PER_WORD + h] = f[h];
+                    for (int h = 0; h < EL<ST>::PER_WORD; ++h) acc.t[i][k * EL<ST>::PER_WORD + h] = f[h];
                 }
             }
         }
@@ -219,7 +232,7 @@ struct Kern {
 #pragma unroll
             for (int i = 0; i < CPL; ++i)
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) acc.v[i][e] += __shfl_xor_sync(FULL, acc.v[i][e], off);
+                for (int e = 0; e < EPV; ++e) acc.t[i][e] += __shfl_xor_sync(FULL, acc.t[i][e], off);
     }
 
     // L2-normalise within a lane group and store the row (group 0 stores in mode 1).
@@ -230,7 +243,7 @@ struct Kern {
         for (int i = 0; i < CPL; ++i) {
             if (i * G + lg < a.chunks) {
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) ss = fmaf(acc.v[i][e], acc.v[i][e], ss);
+                for (int e = 0; e < EPV; ++e) ss = fmaf(acc.t[i][e], acc.t[i][e], ss);
             }
         }
 #pragma unroll
@@ -247,7 +260,7 @@ struct Kern {
                 for (int k = 0; k < W; ++k) {
                     float f[EL<ST>::PER_WORD];
 #pragma unroll
-                    for (int h = 0; h < EL<ST>::PER_WORD; ++h) f[h] = acc.v[i][k * EL<ST>::PER_WORD + h] * inv;
+                    for (int h = 0; h < EL<ST>::PER_WORD; ++h) f[h] = acc.t[i][k * EL<ST>::PER_WORD + h] * inv;
                     set_word(x, k, EL<ST>::pack(f));
                 }
                 st_stream(op + q, x);
@@ -267,6 +280,7 @@ struct Kern {
                 if (HV) mw = __ldcs(a.val + cb + lane);
             }
             for (int j0 = 0; j0 < jh; j0 += P * U) gather_batch(a, acc, mc, mw, j0, jh, g, lg);
+            acc.flush();
         }
     }
 
@@ -310,6 +324,7 @@ struct Kern {
                 const int jl = (int)(k - cb);
                 const int jh = (int)min((int64_t)32, end - cb);
                 for (int j0 = jl; j0 < jh; j0 += P * U) gather_batch(a, acc, mc, mw, j0, jh, g, lg);
+                acc.flush();
                 k = cb + jh;
             }
             reduce_groups(acc);
@@ -334,6 +349,7 @@ struct Kern {
                     if (HV) mw = __ldcs(a.val + cb + lg);
                 }
                 for (int j0 = 0; j0 < jh; j0 += U) gather_batch_group(a, acc, mc, mw, j0, jh, lg, gmask);
+                acc.flush();
             }
             finish_row(a, acc, r, lg, true, gmask);
         }
@@ -357,7 +373,7 @@ struct Kern {
                 const int q = i * G + lg;
                 if (q < a.chunks) {
 #pragma unroll
-                    for (int e = 0; e < EPV; ++e) __stcg(slot + q * EPV + e, acc.v[i][e]);
+                    for (int e = 0; e < EPV; ++e) __stcg(slot + q * EPV + e, acc.t[i][e]);
                 }
             }
         }
@@ -370,7 +386,7 @@ struct Kern {
         // Last arrival: add slots 0..k-1 (group g takes c = g, g+P, ...), then the butterfly.
         __threadfence();
         acc.zero();
-        for (int c = g; c < t.k; c += P) {
+        for (int c = g, m = 0; c < t.k; c += P, ++m) {
             const float* s = a.partials + (base + c) * (int64_t)a.d;
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
@@ -380,7 +396,9 @@ struct Kern {
                     for (int e = 0; e < EPV; ++e) acc.v[i][e] += __ldcg(s + q * EPV + e);
                 }
             }
+            if ((m & 31) == 31) acc.flush();
         }
+        acc.flush();
         reduce_groups(acc);
         finish_row(a, acc, r, lg, g == 0, FULL);
         if (lane == 0) a.split_count[t.b] = 0;  // ready for the next launch
