@@ -41,7 +41,7 @@ WORKLOADS = {
     "small": synth.SMALL,
     # a 1/40 scale copy of the large graph (profiling and quick runs)
     "large_1_40": synth.PowerLawSpec("chung_lu_1M_35M_undirected_d128", 1_025_000, 35_000_000,
-                                     2.0, 75_000.0, False, None, 128, 4),
+                                     2.0, 150_000.0, False, None, 128, 4),
 }
 
 # Bounded CPU sample of each workload for the oracle timing: same generator family, smaller.
