@@ -141,6 +141,44 @@ int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
 /* Number of this library's kernel launches on the context so far. */
 int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free propagation step (this entry point has no counterpart in the paper)
+ * ------------------------------------------------------------------------------------- */
+
+/* One iteration T_out = rownorm_L2(M T_in) that never allocates device memory: no
+ * cudaMalloc/cudaFree, no pool, no library routine that allocates.  It is meant for callers
+ * that may not let this library take device memory on its own: a framework whose
+ * allocator owns all of HBM and hands out fixed budgets, a latency-critical loop that
+ * cannot afford cudaMalloc/cudaFree (which can synchronise the device), or a job that must
+ * not fail with out-of-memory halfway.
+ *
+ * Inputs, all device pointers owned by the caller: the CSR of M (rowptr[n+1] int64,
+ * col[nnz] int32, and val[nnz] FP32 M_ab, or val == NULL for unit weights, where rows are
+ * summed and the normalisation removes the common 1/deg factor), T_in (n x d, storage type)
+ * and the output T_out (n x d, same type, must not overlap T_in).  Results agree with
+ * cleora_propagate within the parity tolerances (1e-5 FP32, 2e-2 BF16); the summation order
+ * can differ because rows longer than split_len are split differently.
+ *
+ * Scratch: one file-scope device array of 8,618,240 bytes (cleora_noalloc_limits reports
+ * it), held by every GPU that loads the library until the process exits.  It carries the
+ * work counter, the table of split rows and up to min(16384, 8 MiB / (4 d)) FP32 partial
+ * sums of split rows.  split_len (0 = the smallest allowed, at least 256) must be at least
+ * ceil(2 * nnz / that chunk limit), else the call returns CLEORA_ERR_INVALID_ARG before
+ * launching anything; d must be a multiple of 8 in [8, 1024].
+ *
+ * Every call shares the array and keeps the previous call's contents (the counters are
+ * cleared at the start of each call), so calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race and give wrong results.  Work is queued
+ * on `cuda_stream` (NULL: the legacy default stream) on the current device; the call returns
+ * without waiting.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that first call
+ * before any stream capture.  Out-of-range column indices are skipped, not reported. */
+int cleora_propagate_noalloc(const int64_t* rowptr, const int32_t* col, const float* val,
+                             int64_t n, int64_t nnz, const void* T_in, void* T_out, int d,
+                             cleora_dtype storage, int64_t split_len, void* cuda_stream);
+/* Scratch size in bytes and the largest number of split-row chunks for dimension d. */
+int cleora_noalloc_limits(int d, int64_t* scratch_bytes, int64_t* max_split_chunks);
+
 #ifdef __cplusplus
 }
 #endif

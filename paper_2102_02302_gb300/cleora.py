@@ -57,6 +57,10 @@ SIGNATURES = {
     "cleora_set_option": (ctypes.c_int, [_P, ctypes.c_int, _I64]),
     "cleora_get_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64)]),
     "cleora_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_propagate_noalloc": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P, _P, ctypes.c_int,
+                                                ctypes.c_int, _I64, _P]),
+    "cleora_noalloc_limits": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64),
+                                             ctypes.POINTER(_I64)]),
 }
 
 
@@ -228,6 +232,28 @@ def cleora_launch_count(ctx) -> int:
     v = _I64()
     _check(ctx, load().cleora_launch_count(ctx, ctypes.byref(v)))
     return v.value
+
+
+def cleora_propagate_noalloc(rowptr, col, val, n: int, nnz: int, T_in, T_out, d: int,
+                             storage: str | int = "f32", split_len: int = 0,
+                             stream: int | None = None) -> None:
+    """One allocation-free step on device tensors (see include/cleora.h)."""
+    dt = DTYPES[storage] if isinstance(storage, str) else int(storage)
+    ptrs = [_ptr(x) for x in (rowptr, col, val, T_in, T_out)]
+    if any(p is not None and dev != 1 for p, dev in ptrs):
+        raise ValueError("all arrays must be device tensors")
+    st = load().cleora_propagate_noalloc(ptrs[0][0], ptrs[1][0], ptrs[2][0], int(n), int(nnz),
+                                         ptrs[3][0], ptrs[4][0], int(d), dt, int(split_len), stream)
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_propagate_noalloc: " + load().cleora_status_string(st).decode())
+
+
+def cleora_noalloc_limits(d: int) -> dict:
+    sb, mc = _I64(), _I64()
+    st = load().cleora_noalloc_limits(int(d), ctypes.byref(sb), ctypes.byref(mc))
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_noalloc_limits: invalid d")
+    return {"scratch_bytes": sb.value, "max_split_chunks": mc.value}
 
 
 # ---- convenience object (same calls, owns the handle) ------------------------------------

@@ -39,6 +39,7 @@ struct Args {
     int chunks;      // vectors per row
     int d;
     int64_t split_len;
+    int64_t skip_len = INT64_MAX;  // rows_coop<true> skips longer rows (run as split chunks)
     const Task* tasks;
     int64_t ntasks;
     unsigned long long* counter;
@@ -285,7 +286,9 @@ struct Kern {
     }
 
     // Mode 1: the warp walks rows [rb, re) one at a time; rowptr and column windows are
-    // loaded 32 at a time and reused across consecutive rows.
+    // loaded 32 at a time and reused across consecutive rows.  SKIP: leave out rows longer
+    // than a.skip_len (a caller that runs those rows as split chunks).
+    template <bool SKIP = false>
     __device__ static void rows_coop(const Args& a, int64_t rb, int64_t re, int lane, int g, int lg) {
         int64_t wr = rb, lo = 0, hi = 0;
         if (wr + lane < re) {
@@ -306,6 +309,7 @@ struct Kern {
             }
             const int64_t beg = __shfl_sync(FULL, lo, (int)(r - wr));
             const int64_t end = __shfl_sync(FULL, hi, (int)(r - wr));
+            if (SKIP && end - beg > a.skip_len) continue;
             Acc acc;
             acc.zero();
             if (beg == end) {
