@@ -142,6 +142,57 @@ int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
 int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched small graphs: many independent graphs in one persistent launch per iteration
+ * step (Sec. 4.2-4.3: each relation pair gets its own M, trained independently; the paper
+ * runs them in separate threads)
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct {
+    const uint64_t* src;      /* num_edges ids (host or device, as the batch flag says)     */
+    const uint64_t* dst;
+    const float* weights;     /* NULL: unit weights                                         */
+    int64_t num_edges;        /* >= 0                                                       */
+    int directed;
+    int d;                    /* multiple of 8 in [8, 1024]                                 */
+    int iters;                /* >= 0 iterations for this graph                             */
+    uint64_t seed;            /* init seed (T_0 as in cleora_init)                          */
+    cleora_dtype storage;     /* FP32 or BF16 embeddings                                    */
+} cleora_graph_desc;
+
+typedef struct cleora_batch cleora_batch;
+
+/* Builds every graph exactly as cleora_graph_build would, packs them into one multi-graph
+ * CSR (per-graph node, entry and embedding offsets), picks each graph's kernel schedule
+ * (autotune != 0: the fastest of the candidate vector widths and row modes, timed per
+ * (d, storage) class on a sample of its graphs; 0: the single-graph defaults) and captures
+ * init + every iteration step + the FP32 output pass in one CUDA graph on `cuda_stream`
+ * (NULL: a stream the batch creates).  Graph g's result equals, bit for bit, a single-graph
+ * context given the same schedule options (cleora_batch_schedule reports them).
+ * Errors: CLEORA_ERR_INVALID_ARG (a bad descriptor; *out stays NULL), CLEORA_ERR_OOM. */
+int cleora_batch_create(cleora_batch** out, int device, void* cuda_stream,
+                        const cleora_graph_desc* graphs, int count, int inputs_on_device,
+                        int autotune);
+void cleora_batch_destroy(cleora_batch* b);
+const char* cleora_batch_last_error(const cleora_batch* b);
+/* Totals: nodes, CSR entries, FP32 output elements (sum of n_g * d_g), largest iters. */
+int cleora_batch_totals(const cleora_batch* b, int64_t* nodes, int64_t* nnz,
+                        int64_t* out_elems, int* max_iters);
+/* Graph g: its node count, entries, and the element offset of its n_g x d_g FP32 rows in
+ * the packed output. */
+int cleora_batch_graph_info(const cleora_batch* b, int g, int64_t* n, int64_t* nnz,
+                            int64_t* out_offset);
+/* Schedule chosen for graph g: gather bytes, row mode, split length, task size. */
+int cleora_batch_schedule(const cleora_batch* b, int g, int64_t* vec_bytes, int64_t* row_mode,
+                          int64_t* split_len, int64_t* task_nnz);
+/* ids[n_g] of graph g, ascending. */
+int cleora_batch_node_ids(cleora_batch* b, int g, uint64_t* out, int out_on_device);
+/* Replays the captured graph: T_0, iters_g iterations of every graph, then all results
+ * packed as FP32 into out[out_elems] (host or device).  Returns when `out` is written. */
+int cleora_batch_run(cleora_batch* b, float* out, int out_on_device);
+/* Kernel launches of the last run (the captured graph's kernel nodes). */
+int cleora_batch_launches(const cleora_batch* b, int64_t* launches);
+
+/* ---------------------------------------------------------------------------------------
  * Allocation-free propagation step (this entry point has no counterpart in the paper)
  * ------------------------------------------------------------------------------------- */
 

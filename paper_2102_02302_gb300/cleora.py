@@ -57,6 +57,20 @@ SIGNATURES = {
     "cleora_set_option": (ctypes.c_int, [_P, ctypes.c_int, _I64]),
     "cleora_get_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64)]),
     "cleora_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int]),
+    "cleora_batch_destroy": (None, [_P]),
+    "cleora_batch_last_error": (ctypes.c_char_p, [_P]),
+    "cleora_batch_totals": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                           ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int)]),
+    "cleora_batch_graph_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64),
+                                               ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "cleora_batch_schedule": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64),
+                                             ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                             ctypes.POINTER(_I64)]),
+    "cleora_batch_node_ids": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    "cleora_batch_run": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "cleora_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "cleora_propagate_noalloc": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P, _P, ctypes.c_int,
                                                 ctypes.c_int, _I64, _P]),
     "cleora_noalloc_limits": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64),
@@ -254,6 +268,147 @@ def cleora_noalloc_limits(d: int) -> dict:
     if st != CLEORA_OK:
         raise CleoraError(st, "cleora_noalloc_limits: invalid d")
     return {"scratch_bytes": sb.value, "max_split_chunks": mc.value}
+
+
+# ---- batched small graphs -------------------------------------------------------------
+
+class cleora_graph_desc(ctypes.Structure):
+    _fields_ = [("src", _P), ("dst", _P), ("weights", _P), ("num_edges", _I64),
+                ("directed", ctypes.c_int), ("d", ctypes.c_int), ("iters", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("storage", ctypes.c_int)]
+
+
+def _bcheck(b, status: int):
+    if status != CLEORA_OK:
+        lib = load()
+        msg = lib.cleora_batch_last_error(b).decode() if b else ""
+        raise CleoraError(status, msg or lib.cleora_status_string(status).decode())
+
+
+def cleora_batch_create(graphs, device: int = 0, stream: int | None = None, autotune: bool = True):
+    """graphs: sequence of dicts with src, dst, weights (or None), directed, d, iters, seed,
+    storage; all arrays on the host (numpy) or all on the device (torch CUDA)."""
+    lib = load()
+    descs = (cleora_graph_desc * max(len(graphs), 1))()
+    on_dev = None
+    for i, g in enumerate(graphs):
+        ps, ds = _ptr(g["src"])
+        pd, dd = _ptr(g["dst"])
+        pw, dw = _ptr(g.get("weights"))
+        devs = {ds, dd} | ({dw} if g.get("weights") is not None else set())
+        if len(g["src"]) == 0:
+            devs = set()
+        if len(devs) > 1 or (on_dev is not None and devs and devs != {on_dev}):
+            raise ValueError("all edge arrays must be on the host or all on the device")
+        if devs:
+            on_dev = devs.pop()
+        st = g.get("storage", "f32")
+        descs[i] = cleora_graph_desc(ps, pd, pw, int(len(g["src"])), int(bool(g["directed"])),
+                                     int(g["d"]), int(g["iters"]), int(g.get("seed", 0)) & (2**64 - 1),
+                                     DTYPES[st] if isinstance(st, str) else int(st))
+    h = _P()
+    st = lib.cleora_batch_create(ctypes.byref(h), device, stream, descs, len(graphs), on_dev or 0,
+                                 int(bool(autotune)))
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_batch_create failed: " + lib.cleora_status_string(st).decode())
+    return h
+
+
+def cleora_batch_destroy(b) -> None:
+    load().cleora_batch_destroy(b)
+
+
+def cleora_batch_last_error(b) -> str:
+    return load().cleora_batch_last_error(b).decode()
+
+
+def cleora_batch_totals(b) -> dict:
+    n, nnz, oe = _I64(), _I64(), _I64()
+    mi = ctypes.c_int()
+    _bcheck(b, load().cleora_batch_totals(b, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(oe),
+                                          ctypes.byref(mi)))
+    return {"nodes": n.value, "nnz": nnz.value, "out_elems": oe.value, "max_iters": mi.value}
+
+
+def cleora_batch_graph_info(b, g: int) -> dict:
+    n, nnz, off = _I64(), _I64(), _I64()
+    _bcheck(b, load().cleora_batch_graph_info(b, g, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(off)))
+    return {"n": n.value, "nnz": nnz.value, "out_offset": off.value}
+
+
+def cleora_batch_schedule(b, g: int) -> dict:
+    v, m, s, t = _I64(), _I64(), _I64(), _I64()
+    _bcheck(b, load().cleora_batch_schedule(b, g, ctypes.byref(v), ctypes.byref(m), ctypes.byref(s),
+                                            ctypes.byref(t)))
+    return {"vec_bytes": v.value, "row_mode": m.value, "split_len": s.value, "task_nnz": t.value}
+
+
+def cleora_batch_node_ids(b, g: int, out) -> None:
+    p, dev = _ptr(out)
+    _bcheck(b, load().cleora_batch_node_ids(b, g, p, dev))
+
+
+def cleora_batch_run(b, out=None) -> None:
+    p, dev = _ptr(out)
+    _bcheck(b, load().cleora_batch_run(b, p, dev))
+
+
+def cleora_batch_launches(b) -> int:
+    v = _I64()
+    _bcheck(b, load().cleora_batch_launches(b, ctypes.byref(v)))
+    return v.value
+
+
+class Batch:
+    """Many graphs embedded together (wraps a ``cleora_batch``)."""
+
+    def __init__(self, graphs, device: int = 0, stream: int | None = None, autotune: bool = True):
+        self._keep = graphs  # the inputs must stay alive during create
+        self.handle = cleora_batch_create(graphs, device, stream, autotune)
+        self._keep = None
+        self.count = len(graphs)
+        self.totals = cleora_batch_totals(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cleora_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, out=None):
+        if out is None:
+            out = np.empty(self.totals["out_elems"], np.float32)
+        cleora_batch_run(self.handle, out)
+        return out
+
+    def graph(self, out, g: int, d: int):
+        inf = cleora_batch_graph_info(self.handle, g)
+        return out[inf["out_offset"]: inf["out_offset"] + inf["n"] * d].reshape(inf["n"], d)
+
+    def info(self, g: int) -> dict:
+        return cleora_batch_graph_info(self.handle, g)
+
+    def schedule(self, g: int) -> dict:
+        return cleora_batch_schedule(self.handle, g)
+
+    def node_ids(self, g: int) -> np.ndarray:
+        out = np.empty(cleora_batch_graph_info(self.handle, g)["n"], np.uint64)
+        cleora_batch_node_ids(self.handle, g, out)
+        return out
+
+    def launches(self) -> int:
+        return cleora_batch_launches(self.handle)
 
 
 # ---- convenience object (same calls, owns the handle) ------------------------------------

@@ -46,21 +46,6 @@ void dfree(cleora_ctx* ctx, void* p) {
 
 namespace {
 
-// Makes the context's device current for the duration of a call, then restores the
-// caller's device.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 #define GUARD(ctx)                                                                      \
     if (!(ctx)) return CLEORA_ERR_INVALID_ARG;                                          \
     DeviceGuard guard_((ctx)->device);                                                  \

@@ -1,0 +1,12 @@
+// Batched propagate kernels instantiated for storage type __nv_bfloat16 and 8-byte gathers.
+#include "batch_kernels.cuh"
+
+namespace cleora {
+namespace batch {
+
+cudaError_t launch_batch_bf16_v8(int cpl, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+    return BatchLaunch<__nv_bfloat16, 8>::run(cpl, ba, sms, s, grid);
+}
+
+}  // namespace batch
+}  // namespace cleora

@@ -1,0 +1,12 @@
+// Batched propagate kernels instantiated for storage type float and 16-byte gathers.
+#include "batch_kernels.cuh"
+
+namespace cleora {
+namespace batch {
+
+cudaError_t launch_batch_f32_v16(int cpl, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+    return BatchLaunch<float, 16>::run(cpl, ba, sms, s, grid);
+}
+
+}  // namespace batch
+}  // namespace cleora

@@ -56,6 +56,9 @@ struct Shape {
 
 enum { OPT_COUNT = 5 };
 
+constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
+constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
+
 }  // namespace cleora
 
 struct cleora_ctx {
@@ -119,12 +122,41 @@ inline void dfree_null(cleora_ctx* ctx, T*& p) {
     p = nullptr;
 }
 
+// splitmix64 output function (Steele, Lea & Flood 2014), used by the T_0 hash.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// T_0 value of element j of a row whose prefix is mix(mix(seed) ^ id): 2 (h >> 40) 2^-24 - 1,
+// with every step exact in FP32.
+__device__ __forceinline__ float init_value(uint64_t prefix, uint32_t j) {
+    const uint64_t h = mix64(prefix ^ (uint64_t)j);
+    return (float)(uint32_t)(h >> 40) * 0x1p-23f - 1.0f;
+}
+
 inline unsigned grid_for(int64_t items, int threads, int num_sms) {
     int64_t b = (items + threads - 1) / threads;
     int64_t cap = (int64_t)num_sms * 32;
     if (b > cap) b = cap;
     return (unsigned)(b < 1 ? 1 : b);
 }
+
+// Makes a device current for the duration of a call, then restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // ---- parts implemented in the other translation units --------------------------------
 int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
@@ -137,6 +169,7 @@ int convert_impl(cleora_ctx* ctx, const void* src, cleora_dtype sdt, void* dst, 
                  int64_t count);
 
 Shape choose_shape(const cleora_ctx* ctx, int d, cleora_dtype dt);
+Shape shape_for(int d, cleora_dtype dt, int64_t vec_opt, int64_t mode_opt);
 int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz);
 void plan_release(cleora_ctx* ctx);
 int plan_ensure(cleora_ctx* ctx);

@@ -8,17 +8,6 @@
 namespace cleora {
 namespace {
 
-__device__ __forceinline__ uint64_t mix(uint64_t z) {
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ float init_value(uint64_t prefix, uint32_t j) {
-    const uint64_t h = mix(prefix ^ (uint64_t)j);
-    return (float)(uint32_t)(h >> 40) * 0x1p-23f - 1.0f;  // every step exact
-}
 
 // One 16-byte vector per thread-iteration: 4 FP32 or 8 BF16 elements.
 __global__ void k_init_f32(const uint64_t* ids, int64_t n, int d, uint64_t mseed, float4* T) {
@@ -28,7 +17,7 @@ __global__ void k_init_f32(const uint64_t* ids, int64_t n, int d, uint64_t mseed
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = v / vpr;
         const uint32_t j = (uint32_t)(v - i * vpr) * 4u;
-        const uint64_t p = mix(mseed ^ ids[i]);
+        const uint64_t p = mix64(mseed ^ ids[i]);
         float4 o;
         o.x = init_value(p, j);
         o.y = init_value(p, j + 1);
@@ -45,7 +34,7 @@ __global__ void k_init_bf16(const uint64_t* ids, int64_t n, int d, uint64_t msee
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = v / vpr;
         const uint32_t j = (uint32_t)(v - i * vpr) * 8u;
-        const uint64_t p = mix(mseed ^ ids[i]);
+        const uint64_t p = mix64(mseed ^ ids[i]);
         uint32_t w[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -73,11 +62,7 @@ __global__ void k_bf16_to_f32(const __nv_bfloat16* a, float* b, int64_t count) {
 int init_impl(cleora_ctx* ctx, uint64_t seed) {
     const Graph& g = ctx->g;
     if (g.n == 0) return CLEORA_OK;
-    // mix(seed) is the same for every element; the host computes it once.
-    uint64_t z = seed + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    const uint64_t mseed = z ^ (z >> 31);
+    const uint64_t mseed = mix64(seed);  // the same for every element: computed once
     const int64_t vecs = g.n * (ctx->dtype == CLEORA_F32 ? ctx->d / 4 : ctx->d / 8);
     const unsigned grid = grid_for(vecs, 256, ctx->num_sms);
     if (ctx->dtype == CLEORA_F32)

@@ -18,8 +18,6 @@ namespace cleora {
 namespace {
 
 constexpr int64_t ROW_COST = 8;
-constexpr int64_t DEFAULT_SPLIT_LEN = 8192;
-constexpr int64_t DEFAULT_TASK_NNZ = 4096;
 
 __device__ __forceinline__ int64_t run_key(const int64_t* rowptr, int64_t r, int64_t task_nnz) {
     return (rowptr[r] + ROW_COST * r) / task_nnz;
@@ -91,9 +89,13 @@ int pow2ceil(int v) {
 }  // namespace
 
 Shape choose_shape(const cleora_ctx* ctx, int d, cleora_dtype dt) {
+    return shape_for(d, dt, ctx->opt[CLEORA_OPT_VEC_BYTES], ctx->opt[CLEORA_OPT_ROW_MODE]);
+}
+
+Shape shape_for(int d, cleora_dtype dt, int64_t vec_opt, int64_t mode_opt) {
     Shape sh;
     const int es = dt == CLEORA_F32 ? 4 : 2;
-    int vec = ctx->opt[CLEORA_OPT_VEC_BYTES] == 8 ? 8 : 16;
+    int vec = vec_opt == 8 ? 8 : 16;
     int chunks = d * es / vec;
     if (vec == 8 && pow2ceil((chunks + 31) / 32) > 8) {  // too many vectors per lane
         vec = 16;
@@ -108,8 +110,7 @@ Shape choose_shape(const cleora_ctx* ctx, int d, cleora_dtype dt) {
         sh.G = 32;
         sh.cpl = pow2ceil((chunks + 31) / 32);
     }
-    const int64_t m = ctx->opt[CLEORA_OPT_ROW_MODE];
-    sh.mode = (m == 2 && sh.G < 32) ? 2 : 1;
+    sh.mode = (mode_opt == 2 && sh.G < 32) ? 2 : 1;
     return sh;
 }
 

@@ -1,0 +1,118 @@
+"""Batched path (many graphs in one persistent launch per step, CUDA-graph replay).
+
+Each graph's result in the batch must equal, bit for bit, a single-graph context run with
+the schedule the batch chose for it (the per-graph schedule depends on that graph alone),
+and must match the FP64 oracle within the FP32 / BF16 tolerances.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+BF16_TOL = 2e-2
+
+
+def _bf16_round(x):
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint32)
+    return (r << 16).view(np.float32).astype(np.float64)
+
+
+def _mixed_graphs():
+    rs = np.random.default_rng(3)
+    out = []
+    specs = synth.batch_specs(16, seed=5, n_lo=50, n_hi=3000)
+    for k, sp in enumerate(specs):
+        e = sp.generate()
+        out.append((e, sp.d, sp.iters, 1000 + k, "bf16" if k % 2 else "f32"))
+    out.append((synth.random_multigraph(400, 3000, 1, False, False), 96, 4, 7, "f32"))
+    out.append((synth.random_multigraph(300, 500, 2, True, True), 8, 2, 8, "f32"))
+    out.append((synth.random_multigraph(300, 2500, 3, True, False), 64, 1, 9, "bf16"))
+    out.append((synth.star(12000, seed=4), 128, 3, 10, "f32"))        # split rows
+    out.append((synth.star(9000, seed=6), 256, 4, 11, "bf16"))        # split rows, BF16
+    out.append((synth.from_index_pairs([], [], False, n=1), 16, 3, 12, "f32"))  # empty graph
+    out.append((synth.random_multigraph(200, 900, 4, False, True), 1024, 2, 13, "f32"))
+    out.append((synth.random_multigraph(150, 700, 5, True, True), 40, 0, 14, "bf16"))  # iters 0
+    rs.shuffle(out)
+    return out
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    return _mixed_graphs()
+
+
+def _descs(graphs):
+    return [{"src": e.src, "dst": e.dst, "weights": e.weights, "directed": e.directed, "d": d,
+             "iters": it, "seed": seed, "storage": st} for (e, d, it, seed, st) in graphs]
+
+
+def _single(e, d, iters, seed, storage, sched):
+    import paper_2102_02302_gb300 as pkg
+    with pkg.Context(0) as ctx:
+        for k in ("vec_bytes", "row_mode", "split_len", "task_nnz"):
+            ctx.set_option(k, sched[k])
+        ctx.graph_build(e.src, e.dst, e.weights, e.directed)
+        n = ctx.info()["n"]
+        ctx.init(d, seed, storage)
+        out = np.empty((n, d), np.float32)
+        ctx.propagate(iters, out)
+        ctx.sync()
+        return out
+
+
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_equals_single_graph_and_oracle(mixed, autotune):
+    import paper_2102_02302_gb300 as pkg
+    with pkg.Batch(_descs(mixed), autotune=autotune) as b:
+        out = b.run()
+        again = b.run()
+        assert np.array_equal(out, again)  # replay is deterministic
+        assert b.launches() >= 2
+        for g, (e, d, iters, seed, st) in enumerate(mixed):
+            got = b.graph(out, g, d)
+            og = oracle.build_from(e) if e.num_edges else None
+            if og is None:
+                assert got.shape[0] == 0
+                continue
+            assert np.array_equal(b.node_ids(g), og.ids)
+            sched = b.schedule(g)
+            single = _single(e, d, iters, seed, st, sched)
+            assert np.array_equal(got, single), f"graph {g} differs from its single-graph run"
+            T0 = oracle.init(og.ids, d, seed)
+            if st == "bf16":
+                T0 = _bf16_round(T0)
+            want = oracle.propagate(og, T0, iters)
+            if st == "bf16" and iters == 0:
+                want = _bf16_round(want)
+            tol = F32_TOL if st == "f32" else BF16_TOL
+            assert np.abs(got.astype(np.float64) - want).max() <= tol
+
+
+def test_batch_device_output_and_totals(mixed):
+    import torch
+    import paper_2102_02302_gb300 as pkg
+    with pkg.Batch(_descs(mixed), autotune=False) as b:
+        tot = b.totals
+        assert tot["nodes"] == sum(oracle.build_from(e).n for (e, *_r) in mixed if e.num_edges)
+        dev = torch.empty(tot["out_elems"], dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        b.run(dev)
+        host = b.run()
+        assert np.array_equal(dev.cpu().numpy(), host)
+
+
+def test_batch_rejects_bad_descriptors():
+    import paper_2102_02302_gb300 as pkg
+    e = synth.random_multigraph(20, 40, 1, True, False)
+    bad = [{"src": e.src, "dst": e.dst, "weights": None, "directed": True, "d": 12, "iters": 2}]
+    with pytest.raises(pkg.CleoraError):
+        pkg.Batch(bad)
+    bad[0]["d"] = 16
+    bad[0]["iters"] = -1
+    with pytest.raises(pkg.CleoraError):
+        pkg.Batch(bad)
