@@ -274,20 +274,105 @@ def e2e_measure(pkg, spec, host_edges, storage, steps, device):
     return float(np.median(times)), h2d, d2h
 
 
+# ---------------------------------------------------------------------------------------
+# Batched small graphs (4096 graphs, one persistent launch per step, CUDA-graph replay)
+# ---------------------------------------------------------------------------------------
+
+def _gen_batch_chunk(specs):
+    out = []
+    for sp in specs:
+        e = sp.generate()
+        out.append((e.src, e.dst, e.weights, e.directed))
+    return out
+
+
+def generate_batch(count=4096, seed=0, workers=None):
+    """The batched workload: n log-uniform in [50, 50000], average degree U[4, 30], directed
+    with probability 1/2, uniform(0.1, 1) weights, d in {64, 128, 256}, I in {3, 4, 5}."""
+    import multiprocessing as mp
+    specs = synth.batch_specs(count, seed)
+    workers = workers or min(16, os.cpu_count() or 1)
+    chunks = [specs[i::workers] for i in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:  # spawn: safe next to CUDA
+        parts = pool.map(_gen_batch_chunk, chunks)
+    edges = [None] * count
+    for w, part in enumerate(parts):
+        for k, e in enumerate(part):
+            edges[w + k * workers] = e
+    return specs, edges
+
+
+def batch_measure(device, steps, warmup, count=4096):
+    import torch
+    import paper_2102_02302_gb300 as pkg
+    t = time.perf_counter()
+    specs, edges = generate_batch(count)
+    gen_s = time.perf_counter() - t
+    descs = [{"src": e[0], "dst": e[1], "weights": e[2], "directed": e[3], "d": sp.d,
+              "iters": sp.iters, "seed": sp.seed, "storage": "bf16"} for sp, e in zip(specs, edges)]
+    stream = torch.cuda.Stream(device)
+    t = time.perf_counter()
+    with pkg.Batch(descs, device, stream.cuda_stream, autotune=True) as b:
+        create_s = time.perf_counter() - t
+        del descs, edges
+        tot = b.totals
+        work = 0
+        sched = {}
+        for g, sp in enumerate(specs):
+            inf = b.info(g)
+            work += inf["nnz"] * sp.d * sp.iters
+            sched.setdefault(f"bf16_d{sp.d}", b.schedule(g))
+        for _ in range(warmup):
+            b.run(None)
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.cleora_batch_run(b.handle, None)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        run_ms = float(np.median(times))
+        launches = b.launches()
+    return {"graphs": count, "storage": "bf16", "nodes": tot["nodes"], "nnz": tot["nnz"],
+            "nnz_d_iters": work, "value": work / (run_ms * 1e-3), "unit": "nnz*d/s per iteration",
+            "run_ms": run_ms, "launches_per_run": launches, "max_iters": tot["max_iters"],
+            "schedules": sched, "generate_s": gen_s, "create_s": create_s,
+            "value_def": "sum over graphs of nnz*d*I / CUDA-graph replay time (init, all steps, FP32 output)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["batch"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--storage", default="both", choices=["both", "bf16", "f32"])
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        import torch
+        rank, local_rank, world = env_rank()
+        torch.cuda.set_device(local_rank)
+        r = batch_measure(local_rank, args.steps, args.warmup, args.batch_count)
+        if rank == 0:
+            print(json.dumps({"metric": "nnz*d/s per iteration", "value": r["value"],
+                              "unit": "nnz*d/s", "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": r["run_ms"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                              "dtype": "bf16", "data": "synthetic",
+                              "config": {"workload": f"batched_{args.batch_count}_chung_lu_graphs"},
+                              "batched": r}), flush=True)
+        return 0
 
     import torch
     import paper_2102_02302_gb300 as pkg
@@ -371,6 +456,11 @@ def main():
                "note": "public C ABI with pinned host buffers: edge upload, build, init, "
                        f"{spec.iters} iterations and FP32 result download per step"}
 
+    batched = None
+    if not args.no_batch:
+        batched = batch_measure(device, args.steps, args.warmup, args.batch_count)
+        batched["value"] *= world
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(args.workload)
@@ -398,6 +488,7 @@ def main():
         "clocks": hs["clocks"],
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batched": batched,
         "breakdown": {st: {k: v for k, v in s.items() if k not in ("clocks",)} for st, s in sums.items()},
     }
     if "bf16" in sums and "f32" in sums:

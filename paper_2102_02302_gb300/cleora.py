@@ -387,8 +387,12 @@ class Batch:
         self.close()
 
     def run(self, out=None):
-        if out is None:
-            out = np.empty(self.totals["out_elems"], np.float32)
+        """Replays the batch; copies the packed FP32 results to `out` when given."""
+        cleora_batch_run(self.handle, out)
+        return out
+
+    def run_host(self) -> np.ndarray:
+        out = np.empty(self.totals["out_elems"], np.float32)
         cleora_batch_run(self.handle, out)
         return out
 

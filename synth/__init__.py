@@ -141,6 +141,16 @@ def undirected_rounds(E: int):
     return lambda need: need + need // 8 + 1024
 
 
+def _sorted_unique(x: np.ndarray) -> np.ndarray:
+    x = np.sort(x)
+    if x.size == 0:
+        return x
+    keep = np.empty(x.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(x[1:], x[:-1], out=keep[1:])
+    return x[keep]
+
+
 def chung_lu_undirected_idx(n: int, E: int, gamma: float, seed: int, max_deg: float,
                             max_rounds: int = 64):
     """Undirected simple power-law graph as sorted unique (u < v) index pairs.
@@ -167,7 +177,7 @@ def chung_lu_undirected_idx(n: int, E: int, gamma: float, seed: int, max_deg: fl
         keep = u != v
         a = np.minimum(u, v)[keep].astype(U64)
         b = np.maximum(u, v)[keep].astype(U64)
-        keys = np.unique(np.concatenate([keys, (a << U64(32)) | b]))
+        keys = _sorted_unique(np.concatenate([keys, (a << U64(32)) | b]))
     u = (keys >> U64(32)).astype(np.int64)
     v = (keys & U64(0xFFFFFFFF)).astype(np.int64)
     return u, v, {"i0": i0, "rounds_counter_end": c}

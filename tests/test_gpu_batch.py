@@ -69,8 +69,8 @@ def _single(e, d, iters, seed, storage, sched):
 def test_batch_equals_single_graph_and_oracle(mixed, autotune):
     import paper_2102_02302_gb300 as pkg
     with pkg.Batch(_descs(mixed), autotune=autotune) as b:
-        out = b.run()
-        again = b.run()
+        out = b.run_host()
+        again = b.run_host()
         assert np.array_equal(out, again)  # replay is deterministic
         assert b.launches() >= 2
         for g, (e, d, iters, seed, st) in enumerate(mixed):
@@ -102,7 +102,7 @@ def test_batch_device_output_and_totals(mixed):
         dev = torch.empty(tot["out_elems"], dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
         b.run(dev)
-        host = b.run()
+        host = b.run_host()
         assert np.array_equal(dev.cpu().numpy(), host)
 
 
