@@ -40,7 +40,8 @@ typedef enum {
     CLEORA_ERR_STATE = -4,       /* call out of order (e.g. propagate before init)         */
     CLEORA_ERR_TIMEOUT = -5,     /* a bounded wait ran out                                 */
     CLEORA_ERR_REJECTED = -6,    /* serving: the job can never fit the memory budget       */
-    CLEORA_ERR_DEVICE = -7       /* a kernel reported an inconsistency through its flag    */
+    CLEORA_ERR_DEVICE = -7,      /* a kernel reported an inconsistency through its flag    */
+    CLEORA_ERR_CANCELLED = -8    /* serving: the job was cancelled before it started       */
 } cleora_status;
 
 typedef enum { CLEORA_F32 = 0, CLEORA_BF16 = 1 } cleora_dtype;
@@ -191,6 +192,75 @@ int cleora_batch_node_ids(cleora_batch* b, int g, uint64_t* out, int out_on_devi
 int cleora_batch_run(cleora_batch* b, float* out, int out_on_device);
 /* Kernel launches of the last run (the captured graph's kernel nodes). */
 int cleora_batch_launches(const cleora_batch* b, int64_t* launches);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop for embedding jobs of different sizes
+ * (the whole method -- build, init, I iterations -- per job; Sec. 4.5's linear memory model
+ * is what admission budgets against)
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct cleora_server cleora_server;
+
+typedef struct {
+    int device;
+    int64_t hbm_budget_bytes;  /* device bytes the running jobs may hold together;
+                                  0: 80% of the free memory at creation                   */
+    int max_slots;             /* jobs resident and running at once (one stream each); 0: 4 */
+    int queue_capacity;        /* waiting jobs accepted; 0: unbounded                       */
+    int inject_alloc_failure_every; /* test hook: every k-th admitted job gets a failing
+                                       allocation (reported as CLEORA_ERR_OOM); 0: off      */
+} cleora_server_config;
+
+typedef struct {
+    const uint64_t* src;   /* host arrays; they must stay valid until the job is done       */
+    const uint64_t* dst;
+    const float* weights;  /* NULL: unit weights                                            */
+    int64_t num_edges;
+    int directed;
+    int d;                 /* multiple of 8 in [8, 1024]                                    */
+    int iters;             /* >= 0                                                          */
+    uint64_t seed;
+    cleora_dtype storage;
+    float* out;            /* host, out_rows x d FP32 (rows in ascending id order); NULL:
+                              the result is computed and dropped                            */
+    int64_t out_rows;      /* capacity of out in rows (must be >= the node count)           */
+    int64_t nodes_hint;    /* node count if known (tightens the memory estimate); 0: <= 2E */
+} cleora_job;
+
+typedef struct {
+    int status;            /* the job's own status: CLEORA_OK or the error it ended with    */
+    int slot;              /* slot that ran it (-1 if it never ran)                         */
+    int64_t n, nnz;
+    int64_t bytes_reserved;/* the admission estimate it was charged                         */
+    double t_submit, t_admit, t_done;  /* seconds on the server's monotonic clock           */
+} cleora_result;
+
+/* Starts the server: max_slots worker threads, each with its own context and stream, on
+ * `device`.  Admission: a waiting job starts when a slot is free and its estimated peak
+ * device bytes (cleora_serve_estimate) fit in the budget next to the running jobs; jobs are
+ * scanned in arrival order and a later job may start ahead of one that does not fit, unless
+ * that one has been passed over 8 times.  Jobs on different slots overlap on the GPU.  After
+ * a job, its slot returns the memory it held to the driver (pool trim), so the budget
+ * tracks what running jobs hold. */
+int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg);
+/* Queues a job; *job_id identifies it.  CLEORA_ERR_REJECTED: its estimate exceeds the whole
+ * budget, or the queue is full.  CLEORA_ERR_INVALID_ARG: a malformed job. */
+int cleora_serve_submit(cleora_server* s, const cleora_job* job, uint64_t* job_id);
+/* Waits up to timeout_ms (< 0: no limit) for the job; on success fills *result and forgets
+ * the job.  CLEORA_ERR_TIMEOUT: not done yet (poll again).  CLEORA_ERR_INVALID_ARG: unknown
+ * id (or already collected). */
+int cleora_serve_poll(cleora_server* s, uint64_t job_id, int timeout_ms, cleora_result* result);
+/* Cancels a job that has not started (its result status becomes CLEORA_ERR_CANCELLED);
+ * CLEORA_ERR_STATE if it is already running or done. */
+int cleora_serve_cancel(cleora_server* s, uint64_t job_id);
+/* Estimated peak device bytes of a job (graph build, then CSR + two embedding buffers). */
+int64_t cleora_serve_estimate(const cleora_job* job);
+/* Seconds on the server's clock (the clock of cleora_result's timestamps). */
+double cleora_serve_now(const cleora_server* s);
+int cleora_serve_stats(const cleora_server* s, int* queued, int* running, int64_t* bytes_reserved,
+                       int64_t* completed, int64_t* budget);
+/* Stops accepting jobs, cancels waiting ones, waits for running ones, frees everything. */
+void cleora_serve_destroy(cleora_server* s);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free propagation step (this entry point has no counterpart in the paper)

@@ -5,8 +5,8 @@ fills the hash-seeded T_0 ~ U(-1, 1) and runs T_k = rownorm_L2(M T_{k-1}) with h
 sm_103a kernels.  This package only marshals arguments to it.
 """
 from .cleora import *  # noqa: F401,F403
-from .cleora import Batch, Context, CleoraError, load  # noqa: F401
+from .cleora import Batch, Context, CleoraError, Server, load  # noqa: F401
 from . import build_native  # noqa: F401
 
-__all__ = [n for n in dir() if n.startswith("cleora_")] + ["Batch", "Context", "CleoraError", "load",
+__all__ = [n for n in dir() if n.startswith("cleora_")] + ["Batch", "Context", "CleoraError", "Server", "load",
                                                              "build_native"]

@@ -28,6 +28,7 @@ CLEORA_ERR_STATE = -4
 CLEORA_ERR_TIMEOUT = -5
 CLEORA_ERR_REJECTED = -6
 CLEORA_ERR_DEVICE = -7
+CLEORA_ERR_CANCELLED = -8
 
 CLEORA_F32 = 0
 CLEORA_BF16 = 1
@@ -71,6 +72,15 @@ SIGNATURES = {
     "cleora_batch_node_ids": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "cleora_batch_run": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "cleora_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_serve_create": (ctypes.c_int, [ctypes.POINTER(_P), _P]),
+    "cleora_serve_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "cleora_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P]),
+    "cleora_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "cleora_serve_estimate": (_I64, [_P]),
+    "cleora_serve_now": (ctypes.c_double, [_P]),
+    "cleora_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "cleora_serve_destroy": (None, [_P]),
     "cleora_propagate_noalloc": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P, _P, ctypes.c_int,
                                                 ctypes.c_int, _I64, _P]),
     "cleora_noalloc_limits": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64),
@@ -413,6 +423,150 @@ class Batch:
 
     def launches(self) -> int:
         return cleora_batch_launches(self.handle)
+
+
+# ---- serving ---------------------------------------------------------------------------
+
+class cleora_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", _I64), ("max_slots", ctypes.c_int),
+                ("queue_capacity", ctypes.c_int), ("inject_alloc_failure_every", ctypes.c_int)]
+
+
+class cleora_job(ctypes.Structure):
+    _fields_ = [("src", _P), ("dst", _P), ("weights", _P), ("num_edges", _I64),
+                ("directed", ctypes.c_int), ("d", ctypes.c_int), ("iters", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("storage", ctypes.c_int), ("out", _P),
+                ("out_rows", _I64), ("nodes_hint", _I64)]
+
+
+class cleora_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int), ("n", _I64), ("nnz", _I64),
+                ("bytes_reserved", _I64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+def _job_struct(src, dst, weights, directed, d, iters, seed, storage, out, nodes_hint):
+    for x in (src, dst, weights, out):
+        if x is not None and _ptr(x)[1]:
+            raise ValueError("serving jobs take host arrays")
+    st = DTYPES[storage] if isinstance(storage, str) else int(storage)
+    out_rows = 0 if out is None else int(out.shape[0])
+    return cleora_job(_ptr(src)[0], _ptr(dst)[0], _ptr(weights)[0], int(len(src)), int(bool(directed)),
+                      int(d), int(iters), int(seed) & (2**64 - 1), st, _ptr(out)[0], out_rows,
+                      int(nodes_hint))
+
+
+def cleora_serve_create(device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
+                        queue_capacity: int = 0, inject_alloc_failure_every: int = 0):
+    lib = load()
+    cfg = cleora_server_config(device, hbm_budget_bytes, max_slots, queue_capacity,
+                               inject_alloc_failure_every)
+    h = _P()
+    st = lib.cleora_serve_create(ctypes.byref(h), ctypes.byref(cfg))
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_serve_create failed: " + lib.cleora_status_string(st).decode())
+    return h
+
+
+def cleora_serve_submit(server, job: cleora_job) -> int:
+    jid = ctypes.c_uint64()
+    st = load().cleora_serve_submit(server, ctypes.byref(job), ctypes.byref(jid))
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_serve_submit: " + load().cleora_status_string(st).decode())
+    return jid.value
+
+
+def cleora_serve_poll(server, job_id: int, timeout_ms: int = -1):
+    """Returns a cleora_result, or None when the job is not done within timeout_ms."""
+    res = cleora_result()
+    st = load().cleora_serve_poll(server, job_id, int(timeout_ms), ctypes.byref(res))
+    if st == CLEORA_ERR_TIMEOUT:
+        return None
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_serve_poll: " + load().cleora_status_string(st).decode())
+    return res
+
+
+def cleora_serve_cancel(server, job_id: int) -> int:
+    return load().cleora_serve_cancel(server, job_id)
+
+
+def cleora_serve_estimate(job: cleora_job) -> int:
+    return load().cleora_serve_estimate(ctypes.byref(job))
+
+
+def cleora_serve_now(server) -> float:
+    return load().cleora_serve_now(server)
+
+
+def cleora_serve_stats(server) -> dict:
+    q, r = ctypes.c_int(), ctypes.c_int()
+    b, c, bud = _I64(), _I64(), _I64()
+    st = load().cleora_serve_stats(server, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b),
+                                   ctypes.byref(c), ctypes.byref(bud))
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_serve_stats")
+    return {"queued": q.value, "running": r.value, "bytes_reserved": b.value,
+            "completed": c.value, "budget": bud.value}
+
+
+def cleora_serve_destroy(server) -> None:
+    load().cleora_serve_destroy(server)
+
+
+class Server:
+    """Continuous-batching embedding server (wraps a ``cleora_server``)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
+                 queue_capacity: int = 0, inject_alloc_failure_every: int = 0):
+        self.handle = cleora_serve_create(device, hbm_budget_bytes, max_slots, queue_capacity,
+                                          inject_alloc_failure_every)
+        self._held = {}  # job id -> arrays the job reads or writes (kept alive until collected)
+
+    def submit(self, src, dst, weights=None, directed=False, d=128, iters=4, seed=0,
+               storage="f32", out=None, nodes_hint=0) -> int:
+        job = _job_struct(src, dst, weights, directed, d, iters, seed, storage, out, nodes_hint)
+        jid = cleora_serve_submit(self.handle, job)
+        self._held[jid] = (src, dst, weights, out)
+        return jid
+
+    def estimate(self, src, dst, weights=None, directed=False, d=128, iters=4, storage="f32",
+                 nodes_hint=0) -> int:
+        return cleora_serve_estimate(_job_struct(src, dst, weights, directed, d, iters, 0, storage,
+                                                 None, nodes_hint))
+
+    def poll(self, job_id: int, timeout_ms: int = -1):
+        res = cleora_serve_poll(self.handle, job_id, timeout_ms)
+        if res is not None:
+            self._held.pop(job_id, None)
+        return res
+
+    def cancel(self, job_id: int) -> int:
+        return cleora_serve_cancel(self.handle, job_id)
+
+    def now(self) -> float:
+        return cleora_serve_now(self.handle)
+
+    def stats(self) -> dict:
+        return cleora_serve_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cleora_serve_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ---- convenience object (same calls, owns the handle) ------------------------------------

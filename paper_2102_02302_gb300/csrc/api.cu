@@ -30,6 +30,8 @@ int cuda_fail(cleora_ctx* ctx, cudaError_t e, const char* what, const char* file
 
 int dalloc_bytes(cleora_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
+    if (ctx->inject_alloc_fail >= 0 && ctx->inject_alloc_fail-- == 0)
+        return fail(ctx, CLEORA_ERR_OOM, "injected allocation failure (test hook)");
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, ctx->pool, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -138,6 +140,13 @@ int import_T(cleora_ctx* ctx, const void* in, cleora_dtype dtype, int in_on_devi
 }
 
 }  // namespace
+
+void ctx_release_all(cleora_ctx* ctx) {
+    plan_release(ctx);
+    embeddings_release(ctx);
+    graph_release(ctx);
+}
+
 }  // namespace cleora
 
 using namespace cleora;
@@ -154,6 +163,7 @@ const char* cleora_status_string(int status) {
         case CLEORA_ERR_TIMEOUT: return "timed out";
         case CLEORA_ERR_REJECTED: return "rejected";
         case CLEORA_ERR_DEVICE: return "device-reported error";
+        case CLEORA_ERR_CANCELLED: return "cancelled";
         default: return "unknown status";
     }
 }

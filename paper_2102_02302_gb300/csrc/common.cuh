@@ -82,6 +82,7 @@ struct cleora_ctx {
     int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0};
     int* err_flag = nullptr;  // device int, raised by kernels
     int64_t launches = 0;
+    int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails
 };
 
 namespace cleora {
@@ -163,6 +164,8 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
                      const float* w, int64_t E, int directed);
 void graph_release(cleora_ctx* ctx);
 int csr_values_out(cleora_ctx* ctx, float* val_dev);  // M_ab per entry as FP32
+
+void ctx_release_all(cleora_ctx* ctx);  // graph, plan and embeddings of a context
 
 int init_impl(cleora_ctx* ctx, uint64_t seed);
 int convert_impl(cleora_ctx* ctx, const void* src, cleora_dtype sdt, void* dst, cleora_dtype ddt,

@@ -1,0 +1,312 @@
+// Serving runtime (include/cleora.h, cleora_serve_*): a continuous-batching request loop.
+//
+// Slots.  max_slots worker threads, each owning a context (stream + memory pool).  A worker
+// that is free takes the first waiting job that fits: a slot is free and the job's
+// estimated peak device bytes fit in the budget beside the running jobs' reservations.
+// Jobs are scanned in arrival order; a job passed over 8 times blocks further passing, so
+// a large job is not starved.  A job runs the whole method on its slot's stream (upload
+// and build, init, iterations, FP32 result to host), so jobs on different slots overlap on
+// the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver and
+// returns the reservation; waiting workers are woken and admission runs again.
+//
+// Waits are bounded where a caller waits: cleora_serve_poll uses a timed condition wait.
+// Failures are per job (status in its result); the server keeps running.  The allocation
+// failure hook (inject_alloc_failure_every) makes the k-th admitted job's first device
+// allocation fail on the host side, which exercises the OOM path without touching the GPU.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cleora {
+namespace serve {
+
+enum JobState { WAITING, RUNNING, DONE };
+
+struct Job {
+    uint64_t id = 0;
+    cleora_job spec;
+    int64_t est = 0;
+    int bypassed = 0;
+    JobState state = WAITING;
+    cleora_result res;
+};
+
+constexpr int MAX_BYPASS = 8;
+
+}  // namespace serve
+}  // namespace cleora
+
+struct cleora_server {
+    cleora_server_config cfg;
+    int64_t budget = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work;  // workers: a job arrived or memory was returned
+    std::condition_variable cv_done;  // pollers: a job finished
+    std::deque<std::shared_ptr<cleora::serve::Job>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<cleora::serve::Job>> jobs;
+    int64_t reserved = 0;
+    int running = 0;
+    int64_t completed = 0;
+    int64_t admitted = 0;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::vector<cleora_ctx*> slots;
+    std::vector<std::thread> workers;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace cleora {
+namespace serve {
+namespace {
+
+bool valid_job(const cleora_job& j) {
+    return j.num_edges >= 0 && (j.num_edges == 0 || (j.src && j.dst)) && j.d >= 8 && j.d <= 1024 &&
+           j.d % 8 == 0 && j.iters >= 0 && (j.storage == CLEORA_F32 || j.storage == CLEORA_BF16) &&
+           (!j.out || j.out_rows >= 0) && j.nodes_hint >= 0;
+}
+
+// Runs one job on a slot context; returns the job's status.
+int run_job(cleora_server* s, cleora_ctx* ctx, Job& job) {
+    const cleora_job& j = job.spec;
+    int rc = cleora_graph_build(ctx, j.src, j.dst, j.weights, j.num_edges, j.directed, 0);
+    if (rc == CLEORA_OK) {
+        cleora_num_nodes(ctx, &job.res.n);
+        cleora_num_entries(ctx, &job.res.nnz);
+        if (j.out && job.res.n > j.out_rows) rc = CLEORA_ERR_INVALID_ARG;
+    }
+    if (rc == CLEORA_OK) rc = cleora_init(ctx, j.d, j.seed, j.storage);
+    if (rc == CLEORA_OK) rc = cleora_propagate(ctx, j.iters, j.out, 0);
+    if (rc == CLEORA_OK) rc = cleora_sync(ctx);
+    (void)s;
+    return rc;
+}
+
+void worker_main(cleora_server* s, int slot) {
+    cleora_ctx* ctx = s->slots[slot];
+    for (;;) {
+        std::shared_ptr<Job> job;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            for (;;) {
+                if (s->stop) return;
+                // first fit in arrival order, unless the head has been passed over too often
+                for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                    if (s->reserved + (*it)->est <= s->budget) {
+                        job = *it;
+                        s->queue.erase(it);
+                        break;
+                    }
+                    if ((*it)->bypassed >= MAX_BYPASS) break;
+                }
+                if (job) {
+                    for (auto& q : s->queue)  // everyone ahead of it was passed over
+                        if (q->id < job->id) q->bypassed++;
+                    break;
+                }
+                s->cv_work.wait(lk);
+            }
+            s->reserved += job->est;
+            s->running += 1;
+            s->admitted += 1;
+            job->state = RUNNING;
+            job->res.slot = slot;
+            job->res.t_admit = s->now();
+            job->res.bytes_reserved = job->est;
+            const int k = s->cfg.inject_alloc_failure_every;
+            ctx->inject_alloc_fail = (k > 0 && s->admitted % k == 0) ? 0 : -1;
+        }
+        int st = run_job(s, ctx, *job);
+        ctx->inject_alloc_fail = -1;
+        {
+            DeviceGuard guard(ctx->device);
+            ctx_release_all(ctx);
+            cudaStreamSynchronize(ctx->stream);
+            cudaMemPoolTrimTo(ctx->pool, 0);
+            cudaGetLastError();
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            job->res.status = st;
+            job->res.t_done = s->now();
+            job->state = DONE;
+            s->reserved -= job->est;
+            s->running -= 1;
+            s->completed += 1;
+        }
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace serve
+}  // namespace cleora
+
+using namespace cleora;
+using namespace cleora::serve;
+
+extern "C" {
+
+int64_t cleora_serve_estimate(const cleora_job* j) {
+    if (!j) return -1;
+    const int64_t E = j->num_edges;
+    const int64_t m = j->directed ? E : 2 * E;      // CSR entries before dedup (upper bound)
+    const int64_t n = j->nodes_hint > 0 ? j->nodes_hint : std::min<int64_t>(2 * E, ((int64_t)1 << 31) - 1);
+    const int64_t es = j->storage == CLEORA_F32 ? 4 : 2;
+    const int64_t w = j->weights ? 1 : 0;
+    const int64_t MiB = (int64_t)1 << 20;
+    // graph build: uploads, two 2E-key sort buffers, run starts, sorted weights, CSR arrays
+    const int64_t build = E * (16 + 4 * w) + 2 * (2 * E * 8) + (j->directed ? 0 : 8 * m) +
+                          w * 2 * 4 * m + m * (4 + 8 + 4) + n * 32 + 8 * m + 64 * MiB;
+    // resident: CSR (+values), ids, rowptr, degrees; then plan build, then embeddings
+    const int64_t resident = m * 8 + n * (8 + 8 + 4 + 8);
+    const int64_t plan = resident + n * 53 + (m / 64 + 1) * 16;
+    const int64_t prop = resident + (m / 64 + 1) * 16 + 2 * n * j->d * es +
+                         (2 * m / 8192 + 1) * j->d * 4 + (es == 2 ? 256 * MiB : 0) + 64 * MiB;
+    const int64_t peak = std::max(build, std::max(plan, prop));
+    return peak + peak / 10;  // pool rounding and fragmentation
+}
+
+int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
+    if (!out || !cfg || cfg->max_slots < 0 || cfg->queue_capacity < 0 || cfg->hbm_budget_bytes < 0)
+        return CLEORA_ERR_INVALID_ARG;
+    *out = nullptr;
+    cleora_server* s = new (std::nothrow) cleora_server();
+    if (!s) return CLEORA_ERR_OOM;
+    s->cfg = *cfg;
+    if (s->cfg.max_slots == 0) s->cfg.max_slots = 4;
+    s->t0 = std::chrono::steady_clock::now();
+    {
+        DeviceGuard guard(cfg->device);
+        if (!guard.ok) {
+            delete s;
+            return CLEORA_ERR_INVALID_ARG;
+        }
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return CLEORA_ERR_CUDA;
+        }
+        s->budget = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes : (int64_t)(free_b / 10 * 8);
+    }
+    for (int k = 0; k < s->cfg.max_slots; ++k) {
+        cleora_ctx* c = nullptr;
+        int rc = cleora_create(&c, cfg->device, nullptr);
+        if (rc != CLEORA_OK) {
+            for (cleora_ctx* x : s->slots) cleora_destroy(x);
+            delete s;
+            return rc;
+        }
+        s->slots.push_back(c);
+    }
+    for (int k = 0; k < s->cfg.max_slots; ++k) s->workers.emplace_back(worker_main, s, k);
+    *out = s;
+    return CLEORA_OK;
+}
+
+int cleora_serve_submit(cleora_server* s, const cleora_job* job, uint64_t* job_id) {
+    if (!s || !job || !job_id || !valid_job(*job)) return CLEORA_ERR_INVALID_ARG;
+    auto j = std::make_shared<Job>();
+    j->spec = *job;
+    j->est = cleora_serve_estimate(job);
+    j->res = cleora_result();
+    j->res.slot = -1;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return CLEORA_ERR_STATE;
+        if (j->est > s->budget) return CLEORA_ERR_REJECTED;
+        if (s->cfg.queue_capacity > 0 && (int)s->queue.size() >= s->cfg.queue_capacity)
+            return CLEORA_ERR_REJECTED;
+        j->id = s->next_id++;
+        j->res.t_submit = s->now();
+        s->queue.push_back(j);
+        s->jobs[j->id] = j;
+        *job_id = j->id;
+    }
+    s->cv_work.notify_one();
+    return CLEORA_OK;
+}
+
+int cleora_serve_poll(cleora_server* s, uint64_t job_id, int timeout_ms, cleora_result* result) {
+    if (!s || !result) return CLEORA_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return CLEORA_ERR_INVALID_ARG;
+    std::shared_ptr<Job> j = it->second;
+    auto done = [&] { return j->state == DONE; };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, done);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+        return CLEORA_ERR_TIMEOUT;
+    }
+    *result = j->res;
+    s->jobs.erase(job_id);
+    return CLEORA_OK;
+}
+
+int cleora_serve_cancel(cleora_server* s, uint64_t job_id) {
+    if (!s) return CLEORA_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(job_id);
+        if (it == s->jobs.end()) return CLEORA_ERR_INVALID_ARG;
+        std::shared_ptr<Job> j = it->second;
+        if (j->state != WAITING) return CLEORA_ERR_STATE;
+        s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), j), s->queue.end());
+        j->state = DONE;
+        j->res.status = CLEORA_ERR_CANCELLED;
+        j->res.t_done = s->now();
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+    return CLEORA_OK;
+}
+
+double cleora_serve_now(const cleora_server* s) { return s ? s->now() : 0.0; }
+
+int cleora_serve_stats(const cleora_server* s, int* queued, int* running, int64_t* bytes_reserved,
+                       int64_t* completed, int64_t* budget) {
+    if (!s) return CLEORA_ERR_INVALID_ARG;
+    cleora_server* m = const_cast<cleora_server*>(s);
+    std::lock_guard<std::mutex> lk(m->mu);
+    if (queued) *queued = (int)s->queue.size();
+    if (running) *running = s->running;
+    if (bytes_reserved) *bytes_reserved = s->reserved;
+    if (completed) *completed = s->completed;
+    if (budget) *budget = s->budget;
+    return CLEORA_OK;
+}
+
+void cleora_serve_destroy(cleora_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        for (auto& j : s->queue) {
+            j->state = DONE;
+            j->res.status = CLEORA_ERR_CANCELLED;
+            j->res.t_done = s->now();
+        }
+        s->queue.clear();
+    }
+    s->cv_work.notify_all();
+    s->cv_done.notify_all();
+    for (std::thread& t : s->workers) t.join();  // running jobs finish first
+    for (cleora_ctx* c : s->slots) cleora_destroy(c);
+    delete s;
+}
+
+}  // extern "C"
