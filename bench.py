@@ -343,22 +343,199 @@ def batch_measure(device, steps, warmup, count=4096):
             "value_def": "sum over graphs of nnz*d*I / CUDA-graph replay time (init, all steps, FP32 output)"}
 
 
+# ---------------------------------------------------------------------------------------
+# Serving: Poisson arrivals at 80% of measured capacity, p50/p99 arrival -> result on host
+# ---------------------------------------------------------------------------------------
+
+def serve_pool(count=24, seed=0):
+    """Job graphs: n log-uniform in [1e3, 5e6] (quantiles), average degree U[5, 40],
+    undirected unit-weight Chung-Lu (exponent 2.1), generated on the GPU, kept in pinned
+    host memory."""
+    import torch
+    import synth.gpu
+    r = (synth.rng(seed, 200, np.arange(count, dtype=np.uint64)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    pool = []
+    for k in range(count):
+        q = (k + 0.5) / count
+        n = int(round(math.exp(math.log(1e3) + q * (math.log(5e6) - math.log(1e3)))))
+        deg = 5.0 + 35.0 * r[k]
+        E = max(1, int(n * deg / 2))
+        src, dst, meta = synth.gpu.chung_lu_undirected(n, E, 2.1, seed * 1000 + k, max(10.0, 0.02 * 2 * E))
+        pool.append({"n": n, "src": src.cpu().pin_memory(), "dst": dst.cpu().pin_memory(), "edges": meta["edges"]})
+        del src, dst
+    torch.cuda.empty_cache()
+    return pool
+
+
+def serve_jobs(pool, count, seed):
+    cnt = np.arange(count, dtype=np.uint64)
+    u = [(synth.rng(seed, 300 + k, cnt) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 for k in range(4)]
+    logs = np.log([p["n"] for p in pool])
+    jobs = []
+    for i in range(count):
+        ln = math.log(1e3) + u[0][i] * (math.log(5e6) - math.log(1e3))
+        g = int(np.argmin(np.abs(logs - ln)))
+        d = (64, 128, 256, 1024)[min(int(u[1][i] * 4), 3)]
+        it = (3, 4, 5)[min(int(u[2][i] * 3), 2)]
+        st = "bf16" if u[3][i] < 0.5 else "f32"
+        jobs.append((g, d, it, st))
+    return jobs
+
+
+class PinnedArena:
+    """First-fit allocator over one pinned host buffer (job outputs land here directly)."""
+
+    def __init__(self, nbytes):
+        import threading
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.np = self.buf.numpy()
+        self.free = [(0, nbytes)]
+        self.cv = threading.Condition()
+
+    def alloc(self, nbytes):
+        nbytes = (nbytes + 255) // 256 * 256
+        for i, (off, size) in enumerate(self.free):
+            if size >= nbytes:
+                if size == nbytes:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (off + nbytes, size - nbytes)
+                return off, nbytes
+        return None
+
+    def release(self, off, nbytes):
+        with self.cv:
+            self.free.append((off, nbytes))
+            self.free.sort()
+            merged = []
+            for o, sz in self.free:
+                if merged and merged[-1][0] + merged[-1][1] == o:
+                    merged[-1] = (merged[-1][0], merged[-1][1] + sz)
+                else:
+                    merged.append((o, sz))
+            self.free = merged
+            self.cv.notify_all()
+
+    def view(self, off, rows, d):
+        return self.np[off: off + rows * d * 4].view(np.float32).reshape(rows, d)
+
+
+def serve_run(srv, pool, arena, jobs, arrivals, start):
+    """Feeds jobs at their arrival times (waiting for output space when the arena is full)
+    and collects them in completion order.  Returns per-job (result, arrival)."""
+    import threading
+    ids, regions, out = {}, {}, {}
+    lock = threading.Lock()
+
+    def feeder():
+        for k, (g, d, it, st) in enumerate(jobs):
+            delay = start + arrivals[k] - srv.now()
+            if delay > 0:
+                time.sleep(delay)
+            p = pool[g]
+            with arena.cv:
+                while (reg := arena.alloc(p["n"] * d * 4)) is None:
+                    arena.cv.wait(0.05)
+            buf = arena.view(reg[0], p["n"], d)
+            jid = srv.submit(p["src"], p["dst"], None, False, d, it, 1000 + k, st, buf, nodes_hint=p["n"])
+            with lock:
+                ids[jid] = k
+                regions[jid] = reg
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    while len(out) < len(jobs):
+        r = srv.next(1000)
+        if r is None:
+            continue
+        jid, res = r
+        with lock:
+            k = ids[jid]
+            reg = regions.pop(jid)
+        arena.release(*reg)
+        out[k] = res
+    th.join()
+    return [out[k] for k in range(len(jobs))]
+
+
+def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0,
+                  arena_bytes=48 << 30):
+    import paper_2102_02302_gb300 as pkg
+    t = time.perf_counter()
+    pool = serve_pool(seed=seed)
+    arena = PinnedArena(arena_bytes)
+    gen_s = time.perf_counter() - t
+    with pkg.Server(device, max_slots=slots) as srv:
+        # capacity: closed loop (every job available at once; output space is the only gate)
+        cap_jobs = serve_jobs(pool, n_capacity, seed + 1)
+        t0 = srv.now()
+        res = serve_run(srv, pool, arena, cap_jobs, np.zeros(n_capacity), t0)
+        done_t = np.sort([r.t_done for r in res])
+        lo, hi = int(0.1 * n_capacity), int(0.9 * n_capacity)  # steady state: middle 80%
+        capacity = (hi - lo) / (done_t[hi] - done_t[lo])
+        # open loop: Poisson arrivals at 80% of capacity
+        lam = 0.8 * capacity
+        jobs = serve_jobs(pool, n_jobs, seed + 2)
+        u = (synth.rng(seed, 400, np.arange(n_jobs, dtype=np.uint64)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        arrivals = np.cumsum(-np.log(1.0 - u) / lam)
+        start = srv.now() + 0.05
+        results = serve_run(srv, pool, arena, jobs, arrivals, start)
+    ok = [r for r in results if r.status == 0]
+    arr = start + arrivals
+    lat = np.array([r.t_done - a for r, a in zip(results, arr)])[warm:]
+    wait = np.array([r.t_admit - a for r, a in zip(results, arr)])[warm:]
+    svc = np.array([r.t_done - r.t_admit for r in results])[warm:]
+    span = max(r.t_done for r in results[warm:]) - arr[warm]
+    work = sum(r.nnz * j[1] * j[2] for r, j in zip(results[warm:], jobs[warm:]))
+    big = np.array([pool[j[0]]["n"] * j[1] for j in jobs])[warm:]
+    q = np.percentile(big, 90)
+    return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "failed": n_jobs - len(ok),
+            "capacity_jobs_per_s": capacity, "lambda_jobs_per_s": lam,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "queue_wait_p50_ms": float(np.percentile(wait, 50) * 1e3),
+            "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
+            "service_p99_ms": float(np.percentile(svc, 99) * 1e3),
+            "p99_ms_largest_10pct": float(np.percentile(lat[big >= q], 99) * 1e3),
+            "p99_ms_other_90pct": float(np.percentile(lat[big < q], 99) * 1e3),
+            "jobs_per_s": (n_jobs - warm) / span, "nnz_d_iters_per_s": work / span,
+            "pool_graphs": len(pool), "setup_s": gen_s, "output_arena_gb": arena_bytes / 2**30,
+            "latency_def": "Poisson arrival time to FP32 result in (pinned) host memory",
+            "job_mix": "n log-uniform [1e3, 5e6] (24-graph pool, nearest n), degree U[5, 40], "
+                       "d in {64,128,256,1024}, I in {3,4,5}, FP32/BF16 50/50"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--storage", default="both", choices=["both", "bf16", "f32"])
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--batch-count", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        import torch
+        rank, local_rank, world = env_rank()
+        torch.cuda.set_device(local_rank)
+        r = serve_measure(local_rank, args.serve_jobs)
+        if rank == 0:
+            print(json.dumps({"metric": "job p50/p99 latency", "value": r["p99_ms"], "unit": "ms",
+                              "n_gpus": world, "steps": args.serve_jobs, "warmup": r["warmup_jobs"],
+                              "ms_per_step": r["mean_ms"], "higher_is_better": False,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
+                              "data": "synthetic", "config": {"workload": "serving_poisson_80pct"},
+                              "serving": r}), flush=True)
+        return 0
     if args.workload == "batch":
         import torch
         rank, local_rank, world = env_rank()
@@ -461,6 +638,10 @@ def main():
         batched = batch_measure(device, args.steps, args.warmup, args.batch_count)
         batched["value"] *= world
 
+    serving = None
+    if not args.no_serve:
+        serving = serve_measure(device, args.serve_jobs)
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(args.workload)
@@ -489,6 +670,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "batched": batched,
+        "serving": serving,
         "breakdown": {st: {k: v for k, v in s.items() if k not in ("clocks",)} for st, s in sums.items()},
     }
     if "bf16" in sums and "f32" in sums:

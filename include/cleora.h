@@ -240,8 +240,9 @@ typedef struct {
  * device bytes (cleora_serve_estimate) fit in the budget next to the running jobs; jobs are
  * scanned in arrival order and a later job may start ahead of one that does not fit, unless
  * that one has been passed over 8 times.  Jobs on different slots overlap on the GPU.  After
- * a job, its slot returns the memory it held to the driver (pool trim), so the budget
- * tracks what running jobs hold. */
+ * a job, its slot returns the memory it held to the driver (pool trim) except a cache of
+ * min(1 GiB, budget / (8 slots)) per slot, which is set aside from the budget, so the budget
+ * tracks what running jobs and the slot caches hold. */
 int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg);
 /* Queues a job; *job_id identifies it.  CLEORA_ERR_REJECTED: its estimate exceeds the whole
  * budget, or the queue is full.  CLEORA_ERR_INVALID_ARG: a malformed job. */
@@ -250,6 +251,10 @@ int cleora_serve_submit(cleora_server* s, const cleora_job* job, uint64_t* job_i
  * the job.  CLEORA_ERR_TIMEOUT: not done yet (poll again).  CLEORA_ERR_INVALID_ARG: unknown
  * id (or already collected). */
 int cleora_serve_poll(cleora_server* s, uint64_t job_id, int timeout_ms, cleora_result* result);
+/* Waits up to timeout_ms (< 0: no limit) for the next finished job not yet collected, in
+ * completion order; fills *job_id and *result and forgets the job.  CLEORA_ERR_TIMEOUT: none
+ * finished in time. */
+int cleora_serve_next(cleora_server* s, int timeout_ms, uint64_t* job_id, cleora_result* result);
 /* Cancels a job that has not started (its result status becomes CLEORA_ERR_CANCELLED);
  * CLEORA_ERR_STATE if it is already running or done. */
 int cleora_serve_cancel(cleora_server* s, uint64_t job_id);

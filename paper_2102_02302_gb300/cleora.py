@@ -76,6 +76,7 @@ SIGNATURES = {
     "cleora_serve_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "cleora_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P]),
     "cleora_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "cleora_serve_next": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _P]),
     "cleora_serve_estimate": (_I64, [_P]),
     "cleora_serve_now": (ctypes.c_double, [_P]),
     "cleora_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -487,6 +488,18 @@ def cleora_serve_poll(server, job_id: int, timeout_ms: int = -1):
     return res
 
 
+def cleora_serve_next(server, timeout_ms: int = -1):
+    """(job_id, cleora_result) of the next finished job, or None after timeout_ms."""
+    jid = ctypes.c_uint64()
+    res = cleora_result()
+    st = load().cleora_serve_next(server, int(timeout_ms), ctypes.byref(jid), ctypes.byref(res))
+    if st == CLEORA_ERR_TIMEOUT:
+        return None
+    if st != CLEORA_OK:
+        raise CleoraError(st, "cleora_serve_next: " + load().cleora_status_string(st).decode())
+    return jid.value, res
+
+
 def cleora_serve_cancel(server, job_id: int) -> int:
     return load().cleora_serve_cancel(server, job_id)
 
@@ -540,6 +553,12 @@ class Server:
         if res is not None:
             self._held.pop(job_id, None)
         return res
+
+    def next(self, timeout_ms: int = -1):
+        r = cleora_serve_next(self.handle, timeout_ms)
+        if r is not None:
+            self._held.pop(r[0], None)
+        return r
 
     def cancel(self, job_id: int) -> int:
         return cleora_serve_cancel(self.handle, job_id)

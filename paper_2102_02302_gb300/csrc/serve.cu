@@ -6,8 +6,9 @@
 // Jobs are scanned in arrival order; a job passed over 8 times blocks further passing, so
 // a large job is not starved.  A job runs the whole method on its slot's stream (upload
 // and build, init, iterations, FP32 result to host), so jobs on different slots overlap on
-// the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver and
-// returns the reservation; waiting workers are woken and admission runs again.
+// the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver down
+// to a small per-slot cache (charged to the budget up front), and returns the reservation;
+// waiting workers are woken and admission runs again.
 //
 // Waits are bounded where a caller waits: cleora_serve_poll uses a timed condition wait.
 // Failures are per job (status in its result); the server keeps running.  The allocation
@@ -46,13 +47,15 @@ constexpr int MAX_BYPASS = 8;
 
 struct cleora_server {
     cleora_server_config cfg;
-    int64_t budget = 0;
+    int64_t budget = 0;      // for running jobs' reservations
+    int64_t slot_cache = 0;  // device bytes each slot's pool may keep between jobs
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work;  // workers: a job arrived or memory was returned
     std::condition_variable cv_done;  // pollers: a job finished
     std::deque<std::shared_ptr<cleora::serve::Job>> queue;
     std::unordered_map<uint64_t, std::shared_ptr<cleora::serve::Job>> jobs;
+    std::deque<uint64_t> finished;  // completion order, for cleora_serve_next
     int64_t reserved = 0;
     int running = 0;
     int64_t completed = 0;
@@ -133,7 +136,7 @@ void worker_main(cleora_server* s, int slot) {
             DeviceGuard guard(ctx->device);
             ctx_release_all(ctx);
             cudaStreamSynchronize(ctx->stream);
-            cudaMemPoolTrimTo(ctx->pool, 0);
+            cudaMemPoolTrimTo(ctx->pool, (size_t)s->slot_cache);
             cudaGetLastError();
         }
         {
@@ -141,6 +144,7 @@ void worker_main(cleora_server* s, int slot) {
             job->res.status = st;
             job->res.t_done = s->now();
             job->state = DONE;
+            s->finished.push_back(job->id);
             s->reserved -= job->est;
             s->running -= 1;
             s->completed += 1;
@@ -200,7 +204,11 @@ int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
             delete s;
             return CLEORA_ERR_CUDA;
         }
-        s->budget = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes : (int64_t)(free_b / 10 * 8);
+        const int64_t total = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes : (int64_t)(free_b / 10 * 8);
+        // each slot keeps up to slot_cache bytes of its pool between jobs (small jobs then
+        // reuse it without new mappings); those bytes come out of the budget
+        s->slot_cache = std::min<int64_t>((int64_t)1 << 30, total / (8 * (int64_t)s->cfg.max_slots));
+        s->budget = total - s->slot_cache * s->cfg.max_slots;
     }
     for (int k = 0; k < s->cfg.max_slots; ++k) {
         cleora_ctx* c = nullptr;
@@ -269,9 +277,30 @@ int cleora_serve_cancel(cleora_server* s, uint64_t job_id) {
         j->state = DONE;
         j->res.status = CLEORA_ERR_CANCELLED;
         j->res.t_done = s->now();
+        s->finished.push_back(j->id);
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
+    return CLEORA_OK;
+}
+
+int cleora_serve_next(cleora_server* s, int timeout_ms, uint64_t* job_id, cleora_result* result) {
+    if (!s || !job_id || !result) return CLEORA_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] {
+        while (!s->finished.empty() && !s->jobs.count(s->finished.front())) s->finished.pop_front();
+        return !s->finished.empty();
+    };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, ready);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        return CLEORA_ERR_TIMEOUT;
+    }
+    const uint64_t id = s->finished.front();
+    s->finished.pop_front();
+    *job_id = id;
+    *result = s->jobs[id]->res;
+    s->jobs.erase(id);
     return CLEORA_OK;
 }
 
@@ -299,6 +328,7 @@ void cleora_serve_destroy(cleora_server* s) {
             j->state = DONE;
             j->res.status = CLEORA_ERR_CANCELLED;
             j->res.t_done = s->now();
+            s->finished.push_back(j->id);
         }
         s->queue.clear();
     }

@@ -130,3 +130,17 @@ def test_cancel_timeout_injected_failure_and_bad_input(jobs):
         jid = srv.submit(e.src, e.dst, w, False, 16, 3)
         r = srv.poll(jid, 60_000)
         assert r.status in (pkg.CLEORA_ERR_INVALID_ARG, pkg.CLEORA_ERR_OOM)
+
+
+def test_next_returns_every_job_once_in_completion_order(jobs):
+    import paper_2102_02302_gb300 as pkg
+    with pkg.Server(0, max_slots=3) as srv:
+        ids = {_submit(srv, j, None) for j in jobs}
+        seen = []
+        while len(seen) < len(ids):
+            r = srv.next(60_000)
+            assert r is not None
+            seen.append(r[0])
+            assert r[1].status == 0
+        assert sorted(seen) == sorted(ids)
+        assert srv.next(0) is None  # nothing left
