@@ -130,12 +130,16 @@ int cleora_set_embeddings(cleora_ctx* ctx, const void* in, cleora_dtype dtype,
  * ------------------------------------------------------------------------------------- */
 
 typedef enum {
-    CLEORA_OPT_VEC_BYTES = 0,    /* 16 or 8: bytes per gathered vector; 0 = automatic     */
+    CLEORA_OPT_VEC_BYTES = 0,    /* 16 or 8: bytes per gathered vector; 0 = automatic
+                                    (16 when a row holds at least 32 such vectors, else 8) */
     CLEORA_OPT_ROW_MODE = 1,     /* 0 automatic, 1 = lane groups split one row's entries,
                                     2 = each lane group owns its own rows                 */
     CLEORA_OPT_SPLIT_LEN = 2,    /* rows longer than this are split across warps (>= 256)  */
     CLEORA_OPT_TASK_NNZ = 3,     /* entries per scheduled task (>= 64)                      */
-    CLEORA_OPT_BLOCKS_PER_SM = 4 /* persistent CTAs per SM; 0 = occupancy limit            */
+    CLEORA_OPT_BLOCKS_PER_SM = 4, /* persistent CTAs per SM; 0 = occupancy limit           */
+    CLEORA_OPT_HOT_BYTES = 5     /* L2 bytes kept for the rows most entries point at (their
+                                    gathers use an evict_last policy, the rest evict_first);
+                                    0 = 72 MiB, 1 = off; applied at cleora_init            */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);

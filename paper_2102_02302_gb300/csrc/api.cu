@@ -336,7 +336,18 @@ int cleora_get_csr(cleora_ctx* ctx, int64_t* rowptr, int32_t* col, float* val, f
         return CLEORA_OK;
     }
     if (rowptr) CL_TRY(copy_out(ctx, rowptr, g.rowptr, (g.n + 1) * sizeof(int64_t), out_on_device));
-    if (col) CL_TRY(copy_out(ctx, col, g.col, g.nnz * sizeof(int32_t), out_on_device));
+    if (col && g.nnz) {  // without the hot-row marks
+        if (out_on_device) {
+            CL_TRY(col_out(ctx, col));
+        } else {
+            int32_t* tmp = nullptr;
+            CL_TRY(dalloc(ctx, &tmp, (size_t)g.nnz));
+            int rc = col_out(ctx, tmp);
+            if (rc == CLEORA_OK) rc = copy_out(ctx, col, tmp, g.nnz * sizeof(int32_t), 0);
+            dfree(ctx, tmp);
+            CL_TRY(rc);
+        }
+    }
     if (inv_deg) CL_TRY(copy_out(ctx, inv_deg, g.inv_deg, g.n * sizeof(float), out_on_device));
     if (deg) CL_TRY(copy_out(ctx, deg, g.deg, g.n * sizeof(double), out_on_device));
     if (val && g.nnz) {
@@ -371,6 +382,7 @@ int cleora_init(cleora_ctx* ctx, int d, uint64_t seed, cleora_dtype storage) {
     }
     int rc = plan_ensure(ctx);
     if (rc == CLEORA_OK) rc = init_impl(ctx, seed);
+    if (rc == CLEORA_OK) rc = hot_mark(ctx);
     if (rc != CLEORA_OK) { embeddings_release(ctx); return rc; }
     ctx->cur = 0;
     ctx->iteration = 0;
@@ -438,6 +450,9 @@ int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value) {
             break;
         case CLEORA_OPT_BLOCKS_PER_SM:
             if (value < 0 || value > 8) return fail(ctx, CLEORA_ERR_INVALID_ARG, "blocks per SM");
+            break;
+        case CLEORA_OPT_HOT_BYTES:
+            if (value < 0) return fail(ctx, CLEORA_ERR_INVALID_ARG, "hot bytes");
             break;
         default:
             return fail(ctx, CLEORA_ERR_INVALID_ARG, "unknown option");

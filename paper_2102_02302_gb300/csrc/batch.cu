@@ -208,7 +208,7 @@ int build_one(cleora_batch* b, const cleora_graph_desc& gd, int on_dev, OneGraph
     og.iters = gd.iters;
     og.seed = gd.seed;
     og.dtype = gd.storage;
-    og.shape = shape_for(gd.d, gd.storage, 16, 1);
+    og.shape = shape_for(gd.d, gd.storage, 0, 1);
     if (gd.num_edges == 0) return CLEORA_OK;
     const uint64_t* s = gd.src;
     const uint64_t* t = gd.dst;

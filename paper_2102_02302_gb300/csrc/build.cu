@@ -27,22 +27,38 @@ __global__ void k_check_weights(const float* w, int64_t E, int* bad) {
     }
 }
 
-__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t x) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
+constexpr int SAMPLE = 64;  // ids per segment of the two-level lookup
+
+// Every SAMPLE-th id: a small table that stays in L2 and narrows each search to one segment.
+__global__ void k_sample_ids(const uint64_t* ids, int64_t n, uint64_t* sample, int64_t ns) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns;
+         i += (int64_t)gridDim.x * blockDim.x)
+        sample[i] = ids[i * SAMPLE];
+}
+
+// Rank of x among the sorted ids (x is one of them): search the sample, then its segment.
+__device__ __forceinline__ int64_t rank_of(const uint64_t* ids, int64_t n, const uint64_t* sample,
+                                           int64_t ns, uint64_t x) {
+    int64_t lo = 0, hi = ns;  // last sample entry <= x
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (sample[mid] <= x) lo = mid; else hi = mid;
     }
-    return lo;
+    int64_t a = lo * SAMPLE, b = min(n, a + SAMPLE);  // first position with ids[pos] >= x
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (ids[mid] < x) a = mid + 1; else b = mid;
+    }
+    return a;
 }
 
 __global__ void k_entries(const uint64_t* src, const uint64_t* dst, const float* w, int64_t E,
-                          int directed, const uint64_t* ids, int64_t n, int bits, uint64_t invalid,
-                          uint64_t* keys, float* vals) {
+                          int directed, const uint64_t* ids, int64_t n, const uint64_t* sample,
+                          int64_t ns, int bits, uint64_t invalid, uint64_t* keys, float* vals) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t a = (uint64_t)lower_bound_u64(ids, n, src[e]);
-        const uint64_t b = (uint64_t)lower_bound_u64(ids, n, dst[e]);
+        const uint64_t a = (uint64_t)rank_of(ids, n, sample, ns, src[e]);
+        const uint64_t b = (uint64_t)rank_of(ids, n, sample, ns, dst[e]);
         if (directed) {
             keys[e] = (a << bits) | b;
             if (vals) vals[e] = w[e];
@@ -109,6 +125,29 @@ __global__ void k_rowptr(const int32_t* row, int64_t nnz, int64_t n, int64_t* ro
     }
 }
 
+// Unweighted graphs: every e_ab is an integer count, so the row sum is exact in any order;
+// one warp per row (integer accumulation) keeps hub rows from becoming stragglers.
+__global__ void k_degree_int(const int64_t* rowptr, const double* e, int64_t n, double* deg,
+                             float* inv_deg, unsigned long long* max_len) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; r < n; r += warps) {
+        const int64_t b = rowptr[r], t = rowptr[r + 1];
+        long long acc = 0;
+        for (int64_t k = b + lane; k < t; k += 32) acc += (long long)e[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            const double s = (double)acc;
+            deg[r] = s;
+            inv_deg[r] = s > 0.0 ? __fdiv_rn(1.0f, __double2float_rn(s)) : 0.0f;
+            atomicMax(max_len, (unsigned long long)(t - b));
+        }
+    }
+}
+
+// Weighted graphs: deg_a is the FP64 sum of e_ab in ascending column order, one thread per
+// row (the order is part of the bit-exact definition of the stored values).
 __global__ void k_degree(const int64_t* rowptr, const double* e, int64_t n, double* deg,
                          float* inv_deg, unsigned long long* max_len) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
@@ -234,8 +273,13 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         CL_TRY(va.alloc((size_t)m));
         CL_TRY(vb.alloc((size_t)m));
     }
-    k_entries<<<grid_for(E, 256, sms), 256, 0, s>>>(src, dst, w, E, directed, g.ids, n, bits,
-                                                   invalid, ka.p, w ? va.p : nullptr);
+    const int64_t ns = (n + SAMPLE - 1) / SAMPLE;
+    DBuf<uint64_t> sample(ctx);
+    CL_TRY(sample.alloc((size_t)ns));
+    k_sample_ids<<<grid_for(ns, 256, sms), 256, 0, s>>>(g.ids, n, sample.p, ns);
+    CL_LAUNCHED(ctx);
+    k_entries<<<grid_for(E, 256, sms), 256, 0, s>>>(src, dst, w, E, directed, g.ids, n, sample.p, ns,
+                                                   bits, invalid, ka.p, w ? va.p : nullptr);
     CL_LAUNCHED(ctx);
 
     // 3. stable sort by (row, col)
@@ -303,8 +347,12 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     CL_LAUNCHED(ctx);
     CL_TRY(dalloc(ctx, &g.deg, (size_t)(n ? n : 1)));
     CL_TRY(dalloc(ctx, &g.inv_deg, (size_t)(n ? n : 1)));
-    k_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg,
-                                                   reinterpret_cast<unsigned long long*>(scal.p + 2));
+    if (w)
+        k_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg,
+                                                       reinterpret_cast<unsigned long long*>(scal.p + 2));
+    else
+        k_degree_int<<<grid_for(n * 32, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg,
+                                                                reinterpret_cast<unsigned long long*>(scal.p + 2));
     CL_LAUNCHED(ctx);
 
     int64_t hv[3] = {0, 0, 0};
@@ -312,6 +360,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     const int not_unit = (int)(hv[1] & 0xffffffff);
     g.max_row_len = hv[2];
+    g.directed = directed != 0;
     g.has_val = (w != nullptr) || not_unit;
 
     // 6. stored values

@@ -37,6 +37,9 @@ struct Graph {
     bool built = false;
     int64_t n = 0, nnz = 0, max_row_len = 0;
     bool has_val = false;
+    bool directed = false;
+    int64_t marked_row_bytes = 0;  // != 0: col bit 31 marks hot rows for this row size
+    int64_t marked_budget = 0;     // ... and this hot-row budget
     uint64_t* ids = nullptr;
     int64_t* rowptr = nullptr;
     int32_t* col = nullptr;
@@ -54,10 +57,11 @@ struct Shape {
     int chunks = 0; // vectors per row
 };
 
-enum { OPT_COUNT = 5 };
+enum { OPT_COUNT = 6 };
 
 constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
 constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
+constexpr int64_t DEFAULT_HOT_BYTES = (int64_t)72 << 20;  // L2 share kept for hot rows
 
 }  // namespace cleora
 
@@ -79,7 +83,7 @@ struct cleora_ctx {
     int cur = 0;
     int iteration = 0;
 
-    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0};
+    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0};
     int* err_flag = nullptr;  // device int, raised by kernels
     int64_t launches = 0;
     int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails
@@ -177,5 +181,7 @@ int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz);
 void plan_release(cleora_ctx* ctx);
 int plan_ensure(cleora_ctx* ctx);
 int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout);
+int hot_mark(cleora_ctx* ctx);                 // mark gathers of hot rows (after init)
+int col_out(cleora_ctx* ctx, int32_t* col_dev); // column indices without the hot bit
 
 }  // namespace cleora

@@ -80,6 +80,58 @@ __global__ void k_plan_fill(const int32_t* brk_rows, int64_t nb, int64_t n, cons
     }
 }
 
+// Quarter-octave bin of a count: 0 for 0, else 1 + floor(4 log2 c), at most 127.
+__device__ __forceinline__ int count_bin(uint32_t c) {
+    if (c == 0) return 0;
+    const float l = __log2f((float)c);
+    const int b = 1 + (int)(4.0f * l);
+    return b > 127 ? 127 : b;
+}
+
+__global__ void k_indegree(const int32_t* col, int64_t nnz, uint32_t* cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + (col[k] & 0x7fffffff), 1u);
+}
+
+__global__ void k_rowlen(const int64_t* rowptr, int64_t n, uint32_t* cnt) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = rowptr[r + 1] - rowptr[r];
+        cnt[r] = (uint32_t)(l > 0xffffffffll ? 0xffffffffll : l);
+    }
+}
+
+// Per-node bin (uint8) and the global histogram of bins.
+__global__ void k_bins(const uint32_t* cnt, int64_t n, uint8_t* bin, unsigned long long* hist) {
+    __shared__ unsigned int h[128];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int b = count_bin(cnt[r]);
+        bin[r] = (uint8_t)b;
+        atomicAdd(h + b, 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 128; i += blockDim.x)
+        if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+__global__ void k_mark(int32_t* col, int64_t nnz, const uint8_t* bin, int threshold) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[k] & 0x7fffffff;
+        col[k] = (bin[c] >= threshold) ? (int32_t)((uint32_t)c | 0x80000000u) : c;
+    }
+}
+
+__global__ void k_unmark_copy(const int32_t* col, int64_t nnz, int32_t* out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = col[k] & 0x7fffffff;
+}
+
 int pow2ceil(int v) {
     int p = 1;
     while (p < v) p <<= 1;
@@ -95,7 +147,10 @@ Shape choose_shape(const cleora_ctx* ctx, int d, cleora_dtype dt) {
 Shape shape_for(int d, cleora_dtype dt, int64_t vec_opt, int64_t mode_opt) {
     Shape sh;
     const int es = dt == CLEORA_F32 ? 4 : 2;
-    int vec = vec_opt == 8 ? 8 : 16;
+    // automatic width: 16-byte vectors when a row has at least 32 of them (a full warp),
+    // else 8-byte vectors, which put more lanes on a row (measured: BF16 d = 128 runs 8%
+    // faster as a full warp of 8-byte gathers than as half-warps of 16-byte gathers)
+    int vec = vec_opt == 8 ? 8 : vec_opt == 16 ? 16 : (d * es / 16 >= 32 ? 16 : 8);
     int chunks = d * es / vec;
     if (vec == 8 && pow2ceil((chunks + 31) / 32) > 8) {  // too many vectors per lane
         vec = 16;
@@ -224,6 +279,83 @@ int plan_ensure(cleora_ctx* ctx) {
     return CLEORA_OK;
 }
 
+// Marks (bit 31 of col) the entries that point at the rows with the largest in-degree, as
+// many rows as fit in the hot-row L2 budget at the current row size.  Gathers of marked rows
+// are issued with an L2 evict_last policy, the others evict_first, so the rows that most
+// entries share stay in L2 while the long tail streams through.  Graphs whose whole T fits
+// twice in the budget are left unmarked (everything is reused anyway).
+int hot_mark(cleora_ctx* ctx) {
+    Graph& g = ctx->g;
+    const int64_t row_bytes = (int64_t)ctx->d * (ctx->dtype == CLEORA_F32 ? 4 : 2);
+    const int64_t opt = ctx->opt[CLEORA_OPT_HOT_BYTES];
+    const int64_t budget = opt == 0 ? DEFAULT_HOT_BYTES : (opt == 1 ? 0 : opt);
+    // BF16 gathers are issued without cache policies (see the kernel's tuning notes)
+    const bool want = ctx->dtype == CLEORA_F32 && budget > 0 && g.n > 0 && g.n * row_bytes > 2 * budget;
+    const int target = want ? 1 : 0;
+    if (!want && g.marked_row_bytes == 0) return CLEORA_OK;
+    if (want && g.marked_row_bytes == row_bytes && g.marked_budget == budget) return CLEORA_OK;
+    cudaStream_t s = ctx->stream;
+    const int sms = ctx->num_sms;
+    int threshold = 128;  // none hot
+    uint32_t* cnt = nullptr;
+    uint8_t* bin = nullptr;
+    unsigned long long* hist = nullptr;
+    int rc = CLEORA_OK;
+    do {
+        if (target) {
+            if ((rc = dalloc(ctx, &cnt, (size_t)g.n))) break;
+            if ((rc = dalloc(ctx, &bin, (size_t)g.n))) break;
+            if ((rc = dalloc(ctx, &hist, 128))) break;
+            cudaError_t e = cudaMemsetAsync(hist, 0, 128 * sizeof(unsigned long long), s);
+            if (e == cudaSuccess && g.directed) e = cudaMemsetAsync(cnt, 0, g.n * sizeof(uint32_t), s);
+            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot mark", __FILE__, __LINE__); break; }
+            if (g.directed)
+                k_indegree<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, cnt);
+            else  // symmetric: in-degree = row length
+                k_rowlen<<<grid_for(g.n, 256, sms), 256, 0, s>>>(g.rowptr, g.n, cnt);
+            k_bins<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, g.n, bin, hist);
+            ctx->launches += 2;
+            unsigned long long h[128];
+            e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot mark", __FILE__, __LINE__); break; }
+            const int64_t rows = budget / row_bytes;
+            int64_t acc = 0;
+            for (int b = 127; b >= 1; --b) {  // whole bins, from the hottest down
+                if (acc + (int64_t)h[b] > rows) break;
+                acc += (int64_t)h[b];
+                threshold = b;
+            }
+            if (threshold == 128) { rc = CLEORA_OK; }
+        }
+        if (target && threshold < 128) {
+            k_mark<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, threshold);
+            ctx->launches++;
+            g.marked_row_bytes = row_bytes;
+            g.marked_budget = budget;
+        } else if (g.marked_row_bytes != 0) {
+            k_unmark_copy<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, g.col);
+            ctx->launches++;
+            g.marked_row_bytes = 0;
+            g.marked_budget = 0;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "hot mark", __FILE__, __LINE__);
+    } while (0);
+    dfree(ctx, cnt);
+    dfree(ctx, bin);
+    dfree(ctx, hist);
+    return rc;
+}
+
+int col_out(cleora_ctx* ctx, int32_t* col_dev) {
+    const Graph& g = ctx->g;
+    if (g.nnz == 0) return CLEORA_OK;
+    k_unmark_copy<<<grid_for(g.nnz, 256, ctx->num_sms), 256, 0, ctx->stream>>>(g.col, g.nnz, col_dev);
+    CL_LAUNCHED(ctx);
+    return CLEORA_OK;
+}
+
 int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
     const Graph& g = ctx->g;
     const Plan& p = ctx->plan;
@@ -248,6 +380,7 @@ int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
     a.split_count = p.split_count;
     a.partials = p.partials;
     a.err = ctx->err_flag;
+    a.hints = g.marked_row_bytes != 0 ? 1 : 0;
     CL_CUDA(ctx, cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), ctx->stream));
     const int bps = (int)ctx->opt[CLEORA_OPT_BLOCKS_PER_SM];
     cudaError_t e;

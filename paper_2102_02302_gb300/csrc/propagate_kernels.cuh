@@ -22,6 +22,19 @@
 
 #include "common.cuh"
 
+// Compile-time tuning knobs, chosen per storage type from measurements on GB300 (the
+// 1.4B-edge power-law graph, d = 128):
+//   FP32: hot/cold L2 policies on the gathers (-15% time), one batch path, >= 4 CTAs/SM;
+//   BF16: plain gathers (the 64-bit policy registers cost more than they save), a separate
+//         full-batch path, >= 4 CTAs/SM.
+// A -D on the command line overrides the choice for both types (experiments).
+#ifndef CLEORA_INFLIGHT
+#define CLEORA_INFLIGHT 8      // gathered vectors in flight per lane and batch
+#endif
+#ifndef CLEORA_COLD_POLICY
+#define CLEORA_COLD_POLICY 0   // gathers of unmarked rows: 0 evict_first, 1 evict_normal
+#endif
+
 namespace cleora {
 namespace prop {
 
@@ -47,6 +60,65 @@ struct Args {
     int32_t* split_count;
     float* partials;
     int* err;
+    int hints = 0;  // 1: column entries with bit 31 set point at hot rows (keep them in L2)
+};
+
+// L2 policies of the gathers: rows marked hot are loaded evict_last, the rest evict_first
+// (with hints off both are evict_normal).
+struct Pol {
+    uint64_t hot, cold;
+};
+
+__device__ __forceinline__ Pol make_pol(int hints) {
+    Pol p;
+    if (hints) {
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.hot));
+#if CLEORA_COLD_POLICY == 0
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.cold));
+#else
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p.cold));
+#endif
+    } else {
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p.hot));
+        p.cold = p.hot;
+    }
+    return p;
+}
+
+template <typename ST> struct Tune;
+template <> struct Tune<float> {
+#ifdef CLEORA_GATHER_HINTS
+    static constexpr bool HINTS = CLEORA_GATHER_HINTS;
+#else
+    static constexpr bool HINTS = true;
+#endif
+#ifdef CLEORA_FULL_BATCH
+    static constexpr bool FULLB = CLEORA_FULL_BATCH;
+#else
+    static constexpr bool FULLB = false;
+#endif
+#ifdef CLEORA_MIN_BLOCKS
+    static constexpr int MINB = CLEORA_MIN_BLOCKS;
+#else
+    static constexpr int MINB = 4;
+#endif
+};
+template <> struct Tune<__nv_bfloat16> {
+#ifdef CLEORA_GATHER_HINTS
+    static constexpr bool HINTS = CLEORA_GATHER_HINTS;
+#else
+    static constexpr bool HINTS = false;
+#endif
+#ifdef CLEORA_FULL_BATCH
+    static constexpr bool FULLB = CLEORA_FULL_BATCH;
+#else
+    static constexpr bool FULLB = true;
+#endif
+#ifdef CLEORA_MIN_BLOCKS
+    static constexpr int MINB = CLEORA_MIN_BLOCKS;
+#else
+    static constexpr int MINB = 4;
+#endif
 };
 
 template <int VEC> struct VecT;
@@ -62,6 +134,18 @@ __device__ __forceinline__ uint4 ld_gather(const uint4* p) {
 __device__ __forceinline__ uint2 ld_gather(const uint2* p) {
     uint2 r;
     asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint4 ld_gather(const uint4* p, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_gather(const uint2* p, uint64_t pol) {
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+        : "=r"(r.x), "=r"(r.y) : "l"(p), "l"(pol));
     return r;
 }
 __device__ __forceinline__ void st_stream(uint4* p, uint4 v) { __stcs(p, v); }
@@ -97,13 +181,15 @@ template <> struct EL<__nv_bfloat16> {
     }
 };
 
-template <typename ST, int VEC, int CPL, int G, bool HV>
+// CHECK: verify every column index against n (a CSR that does not come from this library's
+// own build); otherwise the index is trusted and only its hot bit is stripped.
+template <typename ST, int VEC, int CPL, int G, bool HV, bool CHECK = false>
 struct Kern {
     using VT = typename VecT<VEC>::T;
     static constexpr int W = VEC / 4;                       // 32-bit words per vector
     static constexpr int EPV = W * EL<ST>::PER_WORD;        // elements per vector
     static constexpr int P = 32 / G;                        // lane groups per warp
-    static constexpr int U = CPL >= 8 ? 1 : 8 / CPL;        // entries in flight per group
+    static constexpr int U = CPL >= CLEORA_INFLIGHT ? 1 : CLEORA_INFLIGHT / CPL;  // entries per batch
 
     // Two-level sum: `v` collects at most one 32-entry window, then is added into `t`.  Every
     // serial FP32 chain stays short (window + windows-per-row) even for a row of thousands of
@@ -149,62 +235,89 @@ struct Kern {
     }
 
     // Entries j = j0 + u*P + g (u < U) of a window of column indices held one per lane
-    // (`mc`, `mw`), restricted to j < jh; all 32 lanes execute the shuffles.
+    // (`mc`, `mw`), restricted to j < jh; all 32 lanes execute the shuffles.  FULLB: every
+    // entry of the batch is valid, so no entry needs a validity test.  Invalid entries load
+    // nothing and add a zero vector (this form also keeps register use lowest).
+    template <bool FULLB>
     __device__ static __forceinline__ void gather_batch(const Args& a, Acc& acc, int mc, float mw,
-                                                        int j0, int jh, int g, int lg) {
+                                                        int j0, int jh, int g, int lg, const Pol& pol) {
         VT x[U][CPL];
         float w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u * P + g;
-            const int c = __shfl_sync(FULL, mc, j & 31);
+            const int raw = __shfl_sync(FULL, mc, j & 31);
             const float wu = HV ? __shfl_sync(FULL, mw, j & 31) : 1.f;
-            bool ok = j < jh;
-            if (ok && (unsigned)c >= (unsigned)a.n) {  // corrupt index: flag, skip
+            bool ok = FULLB || j < jh;
+            const int c = raw & 0x7fffffff;
+            if (CHECK && ok && c >= a.n) {  // corrupt index: flag, skip
                 atomicOr(a.err, 1);
                 ok = false;
             }
             w[u] = ok ? wu : 0.f;
-            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)(ok ? c : 0) * a.row_bytes);
+            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * a.row_bytes) + lg;
+            const uint64_t cp = raw < 0 ? pol.hot : pol.cold;
 #pragma unroll
-            for (int i = 0; i < CPL; ++i) {
-                const int q = i * G + lg;
-                x[u][i] = (ok && q < a.chunks) ? ld_gather(rp + q) : zero_vec();
-            }
+            for (int i = 0; i < CPL; ++i)
+                if (Tune<ST>::HINTS)
+                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G, cp) : zero_vec();
+                else
+                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G) : zero_vec();
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int i = 0; i < CPL; ++i) add_vec(acc, i, x[u][i], w[u]);
+            for (int i = 0; i < CPL; ++i)
+                add_vec(acc, i, x[u][i], w[u]);
     }
 
     // Same for one lane group working alone (mode 2): window of G entries, entries j0+u.
+    template <bool FULLB>
     __device__ static __forceinline__ void gather_batch_group(const Args& a, Acc& acc, int mc, float mw,
-                                                              int j0, int jh, int lg, unsigned gmask) {
+                                                              int j0, int jh, int lg, unsigned gmask,
+                                                              const Pol& pol) {
         VT x[U][CPL];
         float w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u;
-            const int c = __shfl_sync(gmask, mc, j & (G - 1), G);
+            const int raw = __shfl_sync(gmask, mc, j & (G - 1), G);
             const float wu = HV ? __shfl_sync(gmask, mw, j & (G - 1), G) : 1.f;
-            bool ok = j < jh;
-            if (ok && (unsigned)c >= (unsigned)a.n) {
+            bool ok = FULLB || j < jh;
+            const int c = raw & 0x7fffffff;
+            if (CHECK && ok && c >= a.n) {
                 atomicOr(a.err, 1);
                 ok = false;
             }
             w[u] = ok ? wu : 0.f;
-            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)(ok ? c : 0) * a.row_bytes);
+            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * a.row_bytes) + lg;
+            const uint64_t cp = raw < 0 ? pol.hot : pol.cold;
 #pragma unroll
-            for (int i = 0; i < CPL; ++i) {
-                const int q = i * G + lg;
-                x[u][i] = (ok && q < a.chunks) ? ld_gather(rp + q) : zero_vec();
-            }
+            for (int i = 0; i < CPL; ++i)
+                if (Tune<ST>::HINTS)
+                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G, cp) : zero_vec();
+                else
+                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G) : zero_vec();
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int i = 0; i < CPL; ++i) add_vec(acc, i, x[u][i], w[u]);
+            for (int i = 0; i < CPL; ++i)
+                add_vec(acc, i, x[u][i], w[u]);
+    }
+
+    // Entries [jl, jh) of the current window, full batches without predicates.
+    __device__ static __forceinline__ void gather_window(const Args& a, Acc& acc, int mc, float mw, int jl,
+                                                         int jh, int g, int lg, const Pol& pol) {
+        int j0 = jl;
+        if (Tune<ST>::FULLB) {
+#pragma unroll 1
+            for (; j0 + P * U <= jh; j0 += P * U) gather_batch<true>(a, acc, mc, mw, j0, jh, g, lg, pol);
+            if (j0 < jh) gather_batch<false>(a, acc, mc, mw, j0, jh, g, lg, pol);
+        } else {
+#pragma unroll 1
+            for (; j0 < jh; j0 += P * U) gather_batch<false>(a, acc, mc, mw, j0, jh, g, lg, pol);
+        }
     }
 
     // Own previous row (a row without entries keeps it, renormalised).
@@ -271,7 +384,7 @@ struct Kern {
 
     // Accumulate entries [k0, k1) with the whole warp (groups interleave entries).
     __device__ static __forceinline__ void range_coop(const Args& a, Acc& acc, int64_t k0, int64_t k1,
-                                                      int lane, int g, int lg) {
+                                                      int lane, int g, int lg, const Pol& pol) {
         for (int64_t cb = k0; cb < k1; cb += 32) {
             const int jh = (int)min((int64_t)32, k1 - cb);
             int mc = 0;
@@ -280,7 +393,7 @@ struct Kern {
                 mc = __ldcs(a.col + cb + lane);
                 if (HV) mw = __ldcs(a.val + cb + lane);
             }
-            for (int j0 = 0; j0 < jh; j0 += P * U) gather_batch(a, acc, mc, mw, j0, jh, g, lg);
+            gather_window(a, acc, mc, mw, 0, jh, g, lg, pol);
             acc.flush();
         }
     }
@@ -289,7 +402,8 @@ struct Kern {
     // loaded 32 at a time and reused across consecutive rows.  SKIP: leave out rows longer
     // than a.skip_len (a caller that runs those rows as split chunks).
     template <bool SKIP = false>
-    __device__ static void rows_coop(const Args& a, int64_t rb, int64_t re, int lane, int g, int lg) {
+    __device__ static void rows_coop(const Args& a, int64_t rb, int64_t re, int lane, int g, int lg,
+                                     const Pol& pol) {
         int64_t wr = rb, lo = 0, hi = 0;
         if (wr + lane < re) {
             lo = a.rowptr[wr + lane];
@@ -327,7 +441,7 @@ struct Kern {
                 }
                 const int jl = (int)(k - cb);
                 const int jh = (int)min((int64_t)32, end - cb);
-                for (int j0 = jl; j0 < jh; j0 += P * U) gather_batch(a, acc, mc, mw, j0, jh, g, lg);
+                gather_window(a, acc, mc, mw, jl, jh, g, lg, pol);
                 acc.flush();
                 k = cb + jh;
             }
@@ -337,7 +451,7 @@ struct Kern {
     }
 
     // Mode 2: lane group g owns rows rb + g, rb + g + P, ...
-    __device__ static void rows_group(const Args& a, int64_t rb, int64_t re, int g, int lg) {
+    __device__ static void rows_group(const Args& a, int64_t rb, int64_t re, int g, int lg, const Pol& pol) {
         const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (g * G));
         for (int64_t r = rb + g; r < re; r += P) {
             const int64_t beg = a.rowptr[r], end = a.rowptr[r + 1];
@@ -352,7 +466,10 @@ struct Kern {
                     mc = __ldcs(a.col + cb + lg);
                     if (HV) mw = __ldcs(a.val + cb + lg);
                 }
-                for (int j0 = 0; j0 < jh; j0 += U) gather_batch_group(a, acc, mc, mw, j0, jh, lg, gmask);
+                int j0 = 0;
+#pragma unroll 1
+                for (; j0 + U <= jh; j0 += U) gather_batch_group<true>(a, acc, mc, mw, j0, jh, lg, gmask, pol);
+                if (j0 < jh) gather_batch_group<false>(a, acc, mc, mw, j0, jh, lg, gmask, pol);
                 acc.flush();
             }
             finish_row(a, acc, r, lg, true, gmask);
@@ -360,14 +477,14 @@ struct Kern {
     }
 
     // One chunk of a split row; the last chunk to finish combines all partial slots.
-    __device__ static void split_chunk(const Args& a, const Task& t, int lane, int g, int lg) {
+    __device__ static void split_chunk(const Args& a, const Task& t, int lane, int g, int lg, const Pol& pol) {
         const int64_t r = t.a;
         const int64_t beg = a.rowptr[r], end = a.rowptr[r + 1];
         const int64_t k0 = beg + (int64_t)t.c * a.split_len;
         const int64_t k1 = min(end, k0 + a.split_len);
         Acc acc;
         acc.zero();
-        range_coop(a, acc, k0, k1, lane, g, lg);
+        range_coop(a, acc, k0, k1, lane, g, lg, pol);
         reduce_groups(acc);
         const int64_t base = a.split_base[t.b];
         float* slot = a.partials + (base + t.c) * (int64_t)a.d;
@@ -410,10 +527,12 @@ struct Kern {
 };
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
-__global__ void __launch_bounds__(256) k_propagate(Args a) {
+__global__ void __launch_bounds__(256, (Tune<ST>::MINB > 0 && CPL <= 2) ? Tune<ST>::MINB : 1)
+k_propagate(Args a) {
     using K = Kern<ST, VEC, CPL, G, HV>;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
+    const Pol pol = make_pol(a.hints);
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1ull);
@@ -421,11 +540,11 @@ __global__ void __launch_bounds__(256) k_propagate(Args a) {
         if (t >= (unsigned long long)a.ntasks) break;
         const Task task = a.tasks[t];
         if (task.c >= 0) {
-            K::split_chunk(a, task, lane, g, lg);
+            K::split_chunk(a, task, lane, g, lg, pol);
         } else if (MODE == 1 || G == 32) {
-            K::rows_coop(a, task.a, task.b, lane, g, lg);
+            K::rows_coop(a, task.a, task.b, lane, g, lg, pol);
         } else {
-            K::rows_group(a, task.a, task.b, g, lg);
+            K::rows_group(a, task.a, task.b, g, lg, pol);
         }
         __syncwarp();
     }
