@@ -60,6 +60,23 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (identity when not
+    distributed).  CPU tensors for gloo, CUDA tensors for nccl."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Replicas on every rank: units all ranks processed / the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -618,12 +635,8 @@ def main():
             sampler.start()
             r = time_dtype(pkg, ctx, edges, spec, st, args.steps, args.warmup)
             r["clocks"] = sampler.stop()
-            if world > 1:
-                tt = torch.tensor([np.mean(r["step_ms"]), np.median(r["iter_ms"])], device="cuda")
-                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-                r["max_step_ms"], r["max_iter_ms"] = float(tt[0]), float(tt[1])
-            else:
-                r["max_step_ms"], r["max_iter_ms"] = float(np.mean(r["step_ms"])), float(np.median(r["iter_ms"]))
+            r["max_step_ms"], r["max_iter_ms"] = max_over_ranks(
+                [np.mean(r["step_ms"]), np.median(r["iter_ms"])], "cuda")
             results[st] = r
 
     n, nnz, d, hv = info["n"], info["nnz"], spec.d, info["has_val"]
@@ -636,7 +649,7 @@ def main():
         mb = model_bytes(n, nnz, d, es, hv)
         cb = compulsory_bytes(n, nnz, d, es, hv)
         return {
-            "value": world * nnz * d / t_iter,
+            "value": whole_job_rate(nnz * d, world, t_iter),
             "iter_ms_median": r["max_iter_ms"],
             "iter_ms_min": float(np.min(r["iter_ms"])),
             "step_ms": r["max_step_ms"],
