@@ -147,6 +147,40 @@ int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
 int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches);
 
 /* ---------------------------------------------------------------------------------------
+ * Inductivity and additivity (Sec. 1, "Additivity" / "Inductivity"; Sec. 3.2, end;
+ * Algorithm 1, chunks and merge)
+ * ------------------------------------------------------------------------------------- */
+
+/* Rows for nodes added after the embedding (Sec. 1 "Inductivity"; Sec. 3.2: a new node's
+ * embedding is the weighted average of its neighbours' representations, ideally those of
+ * iteration I-1).  Edge k links new node new_ids[k] to existing node nbr_ids[k] with weight
+ * weights[k] (NULL: 1).  With the builder's rules (duplicates merged, e_ub summed in FP64,
+ * M_ub = e_ub / deg_u) each new node u gets rownorm(sum_b M_ub T[b]) over the context's
+ * current embeddings T, computed by the propagation kernel; the context is not modified.
+ * Edges to ids that are not nodes of the graph are dropped (*num_dropped counts them); a new
+ * node with no kept edge gets no row.  Outputs: out_ids[*num_new] ascending and out
+ * (*num_new x d FP32, out_rows capacity; NULL to skip).  Errors: CLEORA_ERR_STATE without
+ * embeddings, CLEORA_ERR_INVALID_ARG for bad weights or too small an output. */
+int cleora_inductive(cleora_ctx* ctx, const uint64_t* new_ids, const uint64_t* nbr_ids,
+                     const float* weights, int64_t num_edges, int inputs_on_device,
+                     uint64_t* out_ids, float* out, int64_t out_rows, int64_t* num_new,
+                     int64_t* num_dropped, int out_on_device);
+
+/* Algorithm 1 with Q = num_chunks edge chunks: edges chunk_offsets[q] .. chunk_offsets[q+1]-1
+ * (host array of Q+1 offsets, chunk_offsets[0] = 0) form chunk q.  Each chunk is embedded on
+ * its own (its own M_q and T_0 from the same id hash, `iters` iterations, `storage`) and
+ * the results are merged: T_v = sum_q w_qv T^q_v with w_qv = occ_q(v) / sum_k occ_k(v), where
+ * occ_q(v) counts the endpoints of chunk q's edges equal to v (the paper's node weight, read
+ * as an occurrence share; a self-loop counts twice).  Q = 1 is the plain method.  Outputs:
+ * out_ids[*num_nodes] (all nodes, ascending id) and out (FP32, out_rows capacity).  The
+ * context's graph and embeddings are replaced by the last chunk's. */
+int cleora_chunked_embed(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
+                         const float* weights, const int64_t* chunk_offsets, int num_chunks,
+                         int directed, int d, int iters, uint64_t seed, cleora_dtype storage,
+                         int inputs_on_device, uint64_t* out_ids, float* out, int64_t out_rows,
+                         int64_t* num_nodes, int out_on_device);
+
+/* ---------------------------------------------------------------------------------------
  * Batched small graphs: many independent graphs in one persistent launch per iteration
  * step (Sec. 4.2-4.3: each relation pair gets its own M, trained independently; the paper
  * runs them in separate threads)

@@ -193,3 +193,64 @@ def embed(edges, d: int, iters: int, seed: int = 0, nthreads: int = 0):
     g = build_from(edges)
     T0 = init(g.ids, d, seed)
     return g, propagate(g, T0, iters, nthreads)
+
+
+def inductive(g: Graph, T, new_ids, nbr_ids, weights=None):
+    """Rows for nodes added after the embedding (Sec. 1, "Inductivity"; Sec. 3.2: a new node
+    is the weighted average of its neighbours' representations).  For every new id u with at
+    least one edge to a node of g: e_ub = weight sum of its edges to b (FP64, edge order),
+    deg_u = sum_b e_ub (ascending b), y = sum_b (e_ub / deg_u) T[b], row = y / ||y||.  Edges to
+    ids that are not nodes of g are dropped.  Returns (ids ascending, rows, dropped)."""
+    T = np.asarray(T, dtype=np.float64)
+    new_ids = np.asarray(new_ids, dtype=np.uint64)
+    nbr_ids = np.asarray(nbr_ids, dtype=np.uint64)
+    w = np.ones(new_ids.size) if weights is None else np.asarray(weights, dtype=np.float32).astype(np.float64)
+    pos = np.searchsorted(g.ids, nbr_ids)
+    known = (pos < g.n) & (g.ids[np.minimum(pos, max(g.n - 1, 0))] == nbr_ids) if g.n else np.zeros(new_ids.size, bool)
+    rows = {}
+    for k in range(new_ids.size):
+        if not known[k]:
+            continue
+        e = rows.setdefault(int(new_ids[k]), {})
+        b = int(pos[k])
+        e[b] = e.get(b, 0.0) + float(w[k])
+    ids = np.array(sorted(rows), dtype=np.uint64)
+    out = np.zeros((ids.size, T.shape[1]))
+    for i, u in enumerate(ids):
+        e = rows[int(u)]
+        deg = 0.0
+        for b in sorted(e):
+            deg += e[b]
+        y = np.zeros(T.shape[1])
+        for b in sorted(e):
+            y += (e[b] / deg) * T[b]
+        nrm = np.sqrt(np.sum(y * y))
+        out[i] = y / nrm if nrm > 0 else 0.0
+    return ids, out, int((~known).sum())
+
+
+def chunked_embed(src, dst, weights, chunk_offsets, directed, d, iters, seed=0):
+    """Algorithm 1 with Q edge chunks: chunk q (edges chunk_offsets[q]..chunk_offsets[q+1]-1)
+    is embedded alone (its own M_q, T_0 from the same id hash, I iterations), then
+    T_v = sum_q w_qv T^q_v with w_qv = occ_q(v) / sum_k occ_k(v), occ_q(v) the number of
+    endpoints of chunk q's edges equal to v (the node weight of Algorithm 1 read as an
+    occurrence share).  Returns (ids ascending, T)."""
+    src = np.asarray(src, dtype=np.uint64)
+    dst = np.asarray(dst, dtype=np.uint64)
+    ids = np.unique(np.concatenate([src, dst]))
+    ends = np.concatenate([src, dst])
+    occ_all = np.zeros(ids.size)
+    np.add.at(occ_all, np.searchsorted(ids, ends), 1.0)
+    acc = np.zeros((ids.size, d))
+    for q in range(len(chunk_offsets) - 1):
+        b, t = int(chunk_offsets[q]), int(chunk_offsets[q + 1])
+        if t == b:
+            continue
+        wq = None if weights is None else np.asarray(weights)[b:t]
+        gq = build_graph(src[b:t], dst[b:t], wq, directed)
+        Tq = propagate(gq, init(gq.ids, d, seed), iters)
+        occ_q = np.zeros(gq.n)
+        np.add.at(occ_q, np.searchsorted(gq.ids, np.concatenate([src[b:t], dst[b:t]])), 1.0)
+        v = np.searchsorted(ids, gq.ids)
+        acc[v] += (occ_q / occ_all[v])[:, None] * Tq
+    return ids, acc

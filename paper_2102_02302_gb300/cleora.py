@@ -59,6 +59,12 @@ SIGNATURES = {
     "cleora_set_option": (ctypes.c_int, [_P, ctypes.c_int, _I64]),
     "cleora_get_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64)]),
     "cleora_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_inductive": (ctypes.c_int, [_P, _P, _P, _P, _I64, ctypes.c_int, _P, _P, _I64,
+                                        ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.c_int]),
+    "cleora_chunked_embed": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_int, _P, _P, _I64, ctypes.POINTER(_I64),
+                                            ctypes.c_int]),
     "cleora_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int]),
     "cleora_batch_destroy": (None, [_P]),
@@ -280,6 +286,41 @@ def cleora_noalloc_limits(d: int) -> dict:
     if st != CLEORA_OK:
         raise CleoraError(st, "cleora_noalloc_limits: invalid d")
     return {"scratch_bytes": sb.value, "max_split_chunks": mc.value}
+
+
+# ---- inductivity and additivity ----------------------------------------------------------
+
+def cleora_inductive(ctx, new_ids, nbr_ids, weights=None, out_ids=None, out=None):
+    """Rows of new nodes from the current embeddings; returns (num_new, num_dropped)."""
+    pn, dn = _ptr(new_ids)
+    pb, _ = _ptr(nbr_ids)
+    pw, _ = _ptr(weights)
+    po, do = _ptr(out)
+    pi, di = _ptr(out_ids)
+    nn, nd = _I64(), _I64()
+    rows = 0 if out is None else int(out.shape[0])
+    _check(ctx, load().cleora_inductive(ctx, pn, pb, pw, int(new_ids.shape[0]), dn, pi, po, rows,
+                                        ctypes.byref(nn), ctypes.byref(nd), do or di))
+    return nn.value, nd.value
+
+
+def cleora_chunked_embed(ctx, src, dst, weights, chunk_offsets, directed, d, iters, seed=0,
+                         storage="f32", out_ids=None, out=None) -> int:
+    """Algorithm 1 with edge chunks; returns the number of nodes."""
+    offs = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+    ps, ds = _ptr(src)
+    pd, _ = _ptr(dst)
+    pw, _ = _ptr(weights)
+    po, do = _ptr(out)
+    pi, di = _ptr(out_ids)
+    nn = _I64()
+    st = DTYPES[storage] if isinstance(storage, str) else int(storage)
+    rows = 0 if out is None else int(out.shape[0])
+    _check(ctx, load().cleora_chunked_embed(ctx, ps, pd, pw, offs.ctypes.data, len(offs) - 1,
+                                            int(bool(directed)), int(d), int(iters),
+                                            int(seed) & (2**64 - 1), st, ds, pi, po, rows,
+                                            ctypes.byref(nn), do or di))
+    return nn.value
 
 
 # ---- batched small graphs -------------------------------------------------------------

@@ -282,15 +282,30 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
                                                    bits, invalid, ka.p, w ? va.p : nullptr);
     CL_LAUNCHED(ctx);
 
-    // 3. stable sort by (row, col)
+    g.directed = directed != 0;
+    return csr_from_entries(ctx, ka.p, kb.p, w ? va.p : nullptr, w ? vb.p : nullptr, m, 2 * E, n, bits,
+                            invalid, g);
+}
+
+int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* vbuf_a, float* vbuf_b,
+                     int64_t m, int64_t kbuf_words, int64_t n, int bits, uint64_t invalid, Graph& g) {
+    cudaStream_t s = ctx->stream;
+    const int sms = ctx->num_sms;
+    const bool weighted = vbuf_a != nullptr;
+    DBuf<int64_t> scal(ctx);  // device scalars: [0] count, [1] flag, [2] max_len, [3] m_valid
+    CL_TRY(scal.alloc(4));
+    CL_CUDA(ctx, cudaMemsetAsync(scal.p, 0, 4 * sizeof(int64_t), s));
+    int* d_flag = reinterpret_cast<int*>(scal.p + 1);
+
+    // stable sort by (row, col)
     uint64_t* keys = nullptr;
     float* vals = nullptr;
     {
-        cub::DoubleBuffer<uint64_t> dk(ka.p, kb.p);
+        cub::DoubleBuffer<uint64_t> dk(kbuf_a, kbuf_b);
         size_t tb = 0;
         DBuf<unsigned char> tmp(ctx);
-        if (w) {
-            cub::DoubleBuffer<float> dv(va.p, vb.p);
+        if (weighted) {
+            cub::DoubleBuffer<float> dv(vbuf_a, vbuf_b);
             CL_CUDA(ctx, cub::DeviceRadixSort::SortPairs(nullptr, tb, dk, dv, m, 0, 2 * bits, s));
             CL_TRY(tmp.alloc(tb));
             CL_CUDA(ctx, cub::DeviceRadixSort::SortPairs(tmp.p, tb, dk, dv, m, 0, 2 * bits, s));
@@ -302,16 +317,14 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         }
         keys = dk.Current();
     }
-    uint64_t* spare = (keys == ka.p) ? kb.p : ka.p;  // free after the sort: reused below
+    uint64_t* spare = (keys == kbuf_a) ? kbuf_b : kbuf_a;  // free after the sort: reused below
 
-    // 4. runs of equal keys
-    uint8_t* head = reinterpret_cast<uint8_t*>(spare);           // m bytes
-    int64_t* start = reinterpret_cast<int64_t*>(spare) + (m + 7) / 8;  // up to m int64
-    // spare holds 2E uint64: m/8 words for flags + m words for starts fits since m <= 2E
-    // only when m/8 + m <= 2E; for directed graphs m = E, for undirected m = 2E and the
-    // starts need their own buffer.
+    // runs of equal keys: head flags (m bytes) and run starts (m int64) share the spare key
+    // buffer when it is large enough
+    uint8_t* head = reinterpret_cast<uint8_t*>(spare);
+    int64_t* start = reinterpret_cast<int64_t*>(spare) + (m + 7) / 8;
     DBuf<int64_t> starts_buf(ctx);
-    if ((m + 7) / 8 + m > 2 * E) {
+    if ((m + 7) / 8 + m > kbuf_words) {
         CL_TRY(starts_buf.alloc((size_t)m));
         start = starts_buf.p;
     }
@@ -341,13 +354,13 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
                                                    rows.p, e.p, d_flag);
     CL_LAUNCHED(ctx);
 
-    // 5. rowptr, degrees
+    // rowptr, degrees
     CL_TRY(dalloc(ctx, &g.rowptr, (size_t)(n + 1)));
     k_rowptr<<<grid_for(nnz + 1, 256, sms), 256, 0, s>>>(rows.p, nnz, n, g.rowptr);
     CL_LAUNCHED(ctx);
     CL_TRY(dalloc(ctx, &g.deg, (size_t)(n ? n : 1)));
     CL_TRY(dalloc(ctx, &g.inv_deg, (size_t)(n ? n : 1)));
-    if (w)
+    if (weighted)
         k_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg,
                                                        reinterpret_cast<unsigned long long*>(scal.p + 2));
     else
@@ -360,10 +373,9 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     const int not_unit = (int)(hv[1] & 0xffffffff);
     g.max_row_len = hv[2];
-    g.directed = directed != 0;
-    g.has_val = (w != nullptr) || not_unit;
+    g.has_val = weighted || not_unit;
 
-    // 6. stored values
+    // stored values
     if (g.has_val) {
         CL_TRY(dalloc(ctx, &g.val, (size_t)(nnz ? nnz : 1)));
         k_values<<<grid_for(nnz, 256, sms), 256, 0, s>>>(rows.p, e.p, g.deg, nnz, g.val);
@@ -371,6 +383,87 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     }
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     g.built = true;
+    return CLEORA_OK;
+}
+
+namespace {
+__global__ void k_rank(const uint64_t* ids, int64_t n, const uint64_t* sample, int64_t ns, const uint64_t* x,
+                       int64_t count, int32_t* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = x[i];
+        int32_t r = -1;
+        if (n > 0 && v >= sample[0]) {
+            const int64_t p = rank_of(ids, n, sample, ns, v);
+            if (p < n && ids[p] == v) r = (int32_t)p;
+        }
+        out[i] = r;
+    }
+}
+}  // namespace
+
+int bit_width_of(int64_t v) { return bit_width(v); }
+
+// Sorted distinct values of keys[count] into a new pool allocation *ids_out (*n_out of them).
+int sort_unique_ids(cleora_ctx* ctx, const uint64_t* keys, int64_t count, uint64_t** ids_out, int64_t* n_out) {
+    cudaStream_t s = ctx->stream;
+    *ids_out = nullptr;
+    *n_out = 0;
+    DBuf<uint64_t> a(ctx), b(ctx);
+    DBuf<int64_t> num(ctx);
+    CL_TRY(a.alloc((size_t)count));
+    CL_TRY(b.alloc((size_t)count));
+    CL_TRY(num.alloc(1));
+    if (count > 0)
+        CL_CUDA(ctx, cudaMemcpyAsync(a.p, keys, count * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    CL_CUDA(ctx, cudaMemsetAsync(num.p, 0, sizeof(int64_t), s));
+    if (count > 0) {
+        cub::DoubleBuffer<uint64_t> db(a.p, b.p);
+        size_t tb = 0, tu = 0;
+        CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(nullptr, tb, db, count, 0, 64, s));
+        CL_CUDA(ctx, cub::DeviceSelect::Unique(nullptr, tu, db.Current(), db.Alternate(), num.p, count, s));
+        DBuf<unsigned char> tmp(ctx);
+        CL_TRY(tmp.alloc(tb > tu ? tb : tu));
+        CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(tmp.p, tb, db, count, 0, 64, s));
+        CL_CUDA(ctx, cub::DeviceSelect::Unique(tmp.p, tu, db.Current(), db.Alternate(), num.p, count, s));
+        int64_t n = 0;
+        CL_CUDA(ctx, cudaMemcpyAsync(&n, num.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, cudaStreamSynchronize(s));
+        CL_TRY(dalloc(ctx, ids_out, (size_t)(n ? n : 1)));
+        CL_CUDA(ctx, cudaMemcpyAsync(*ids_out, db.Alternate(), n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        *n_out = n;
+    } else {
+        CL_TRY(dalloc(ctx, ids_out, 1));
+    }
+    return CLEORA_OK;
+}
+
+int check_weights(cleora_ctx* ctx, const float* w, int64_t E) {
+    if (!w || E == 0) return CLEORA_OK;
+    DBuf<int> flag(ctx);
+    CL_TRY(flag.alloc(1));
+    CL_CUDA(ctx, cudaMemsetAsync(flag.p, 0, sizeof(int), ctx->stream));
+    k_check_weights<<<grid_for(E, 256, ctx->num_sms), 256, 0, ctx->stream>>>(w, E, flag.p);
+    CL_LAUNCHED(ctx);
+    int bad = 0;
+    CL_CUDA(ctx, cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bad) return fail(ctx, CLEORA_ERR_INVALID_ARG, "weights must be finite and > 0");
+    return CLEORA_OK;
+}
+
+int rank_ids(cleora_ctx* ctx, const uint64_t* ids, int64_t n, const uint64_t* x, int64_t count,
+             int32_t* rank_out) {
+    if (count == 0) return CLEORA_OK;
+    const int64_t ns = n > 0 ? (n + SAMPLE - 1) / SAMPLE : 1;
+    DBuf<uint64_t> sample(ctx);
+    CL_TRY(sample.alloc((size_t)ns));
+    if (n > 0) {
+        k_sample_ids<<<grid_for(ns, 256, ctx->num_sms), 256, 0, ctx->stream>>>(ids, n, sample.p, ns);
+        CL_LAUNCHED(ctx);
+    }
+    k_rank<<<grid_for(count, 256, ctx->num_sms), 256, 0, ctx->stream>>>(ids, n, sample.p, ns, x, count, rank_out);
+    CL_LAUNCHED(ctx);
     return CLEORA_OK;
 }
 

@@ -167,6 +167,17 @@ struct DeviceGuard {
 int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
                      const float* w, int64_t E, int directed);
 void graph_release(cleora_ctx* ctx);
+// CSR of M from entry keys (row << bits | col; `invalid` marks dropped entries) and optional
+// FP32 weights (vbuf_a/vbuf_b NULL: unit).  Sorts stably, merges duplicates, fills g's col,
+// rowptr, deg, inv_deg, val, nnz, max_row_len and has_val.  The key buffers (kbuf_words
+// words each) and weight buffers are consumed as scratch.
+int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* vbuf_a, float* vbuf_b,
+                     int64_t m, int64_t kbuf_words, int64_t n, int bits, uint64_t invalid, Graph& g);
+int check_weights(cleora_ctx* ctx, const float* w, int64_t E);  // finite and > 0
+int bit_width_of(int64_t v);
+int sort_unique_ids(cleora_ctx* ctx, const uint64_t* keys, int64_t count, uint64_t** ids_out, int64_t* n_out);
+int rank_ids(cleora_ctx* ctx, const uint64_t* ids, int64_t n, const uint64_t* x, int64_t count,
+             int32_t* rank_out);  // rank of each x among ids, -1 when absent
 int csr_values_out(cleora_ctx* ctx, float* val_dev);  // M_ab per entry as FP32
 
 void ctx_release_all(cleora_ctx* ctx);  // graph, plan and embeddings of a context
