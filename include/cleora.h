@@ -137,14 +137,21 @@ typedef enum {
     CLEORA_OPT_SPLIT_LEN = 2,    /* rows longer than this are split across warps (>= 256)  */
     CLEORA_OPT_TASK_NNZ = 3,     /* entries per scheduled task (>= 64)                      */
     CLEORA_OPT_BLOCKS_PER_SM = 4, /* persistent CTAs per SM; 0 = occupancy limit           */
-    CLEORA_OPT_HOT_BYTES = 5     /* L2 bytes kept for the rows most entries point at (their
-                                    gathers use an evict_last policy, the rest evict_first);
-                                    0 = 72 MiB, 1 = off; applied at cleora_init            */
+    CLEORA_OPT_HOT_BYTES = 5     /* L2 bytes kept for the rows most entries point at:
+                                    cleora_init moves the entries that point at them to the
+                                    front of their rows (gathered with an evict_last
+                                    policy, the rest evict_first) when T is larger than
+                                    twice this; 0 = 72 MiB, 1 = off.  Only the summation
+                                    order changes; cleora_get_csr still returns each row
+                                    in ascending column order                              */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
 /* Number of this library's kernel launches on the context so far. */
 int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches);
+/* Entries that the last cleora_init placed in the hot front part of their rows (see
+ * CLEORA_OPT_HOT_BYTES); 0 when the rows are not partitioned.  ERR_STATE before a graph. */
+int cleora_hot_entries(const cleora_ctx* ctx, int64_t* hot_entries);
 
 /* ---------------------------------------------------------------------------------------
  * Inductivity and additivity (Sec. 1, "Additivity" / "Inductivity"; Sec. 3.2, end;

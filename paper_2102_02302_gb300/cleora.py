@@ -59,6 +59,7 @@ SIGNATURES = {
     "cleora_set_option": (ctypes.c_int, [_P, ctypes.c_int, _I64]),
     "cleora_get_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64)]),
     "cleora_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "cleora_hot_entries": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "cleora_inductive": (ctypes.c_int, [_P, _P, _P, _P, _I64, ctypes.c_int, _P, _P, _I64,
                                         ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.c_int]),
     "cleora_chunked_embed": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int,
@@ -263,6 +264,12 @@ def cleora_get_option(ctx, name: str) -> int:
 def cleora_launch_count(ctx) -> int:
     v = _I64()
     _check(ctx, load().cleora_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def cleora_hot_entries(ctx) -> int:
+    v = _I64()
+    _check(ctx, load().cleora_hot_entries(ctx, ctypes.byref(v)))
     return v.value
 
 
@@ -708,3 +715,6 @@ class Context:
 
     def launches(self) -> int:
         return cleora_launch_count(self.handle)
+
+    def hot_entries(self) -> int:
+        return cleora_hot_entries(self.handle)

@@ -336,7 +336,7 @@ int cleora_get_csr(cleora_ctx* ctx, int64_t* rowptr, int32_t* col, float* val, f
         return CLEORA_OK;
     }
     if (rowptr) CL_TRY(copy_out(ctx, rowptr, g.rowptr, (g.n + 1) * sizeof(int64_t), out_on_device));
-    if (col && g.nnz) {  // without the hot-row marks
+    if (col && g.nnz) {  // ascending column order per row
         if (out_on_device) {
             CL_TRY(col_out(ctx, col));
         } else {
@@ -382,7 +382,7 @@ int cleora_init(cleora_ctx* ctx, int d, uint64_t seed, cleora_dtype storage) {
     }
     int rc = plan_ensure(ctx);
     if (rc == CLEORA_OK) rc = init_impl(ctx, seed);
-    if (rc == CLEORA_OK) rc = hot_mark(ctx);
+    if (rc == CLEORA_OK) rc = hot_partition(ctx);
     if (rc != CLEORA_OK) { embeddings_release(ctx); return rc; }
     ctx->cur = 0;
     ctx->iteration = 0;
@@ -470,6 +470,13 @@ int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value) 
 int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches) {
     if (!ctx || !launches) return CLEORA_ERR_INVALID_ARG;
     *launches = ctx->launches;
+    return CLEORA_OK;
+}
+
+int cleora_hot_entries(const cleora_ctx* ctx, int64_t* hot_entries) {
+    if (!ctx || !hot_entries) return CLEORA_ERR_INVALID_ARG;
+    if (!ctx->g.built) return CLEORA_ERR_STATE;
+    *hot_entries = ctx->g.hot_cnt ? ctx->g.hot_entries : 0;
     return CLEORA_OK;
 }
 

@@ -60,20 +60,19 @@ constexpr int variant_of(int G, int mode, bool hv) {
 }
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
-__device__ __forceinline__ void run_task(const prop::Args& a, const Task& t, int lane, const prop::Pol& pol) {
+__device__ __forceinline__ void run_task(const prop::Args& a, const Task& t, int lane) {
     using K = prop::Kern<ST, VEC, CPL, G, HV>;
     const int g = lane / G, lg = lane % G;
-    if (t.c >= 0) K::split_chunk(a, t, lane, g, lg, pol);
-    else if (MODE == 1 || G == 32) K::rows_coop(a, t.a, t.b, lane, g, lg, pol);
-    else K::rows_group(a, t.a, t.b, g, lg, pol);
+    if (t.c >= 0) K::split_chunk(a, t, lane, g, lg);
+    else if (MODE == 1 || G == 32) K::rows_coop(a, t.a, t.b, lane, g, lg);
+    else K::rows_group(a, t.a, t.b, g, lg);
 }
 
 #define CLEORA_BV(G, MODE, HV) \
-    case variant_of(G, MODE, HV): run_task<ST, VEC, CPL, G, MODE, HV>(a, t, lane, pol); break;
+    case variant_of(G, MODE, HV): run_task<ST, VEC, CPL, G, MODE, HV>(a, t, lane); break;
 
 template <typename ST, int VEC, int CPL>
-__device__ __forceinline__ void dispatch(int variant, const prop::Args& a, const Task& t, int lane,
-                                         const prop::Pol& pol) {
+__device__ __forceinline__ void dispatch(int variant, const prop::Args& a, const Task& t, int lane) {
     if constexpr (CPL == 1) {
         switch (variant) {
             CLEORA_BV(1, 1, false) CLEORA_BV(1, 2, false) CLEORA_BV(2, 1, false) CLEORA_BV(2, 2, false)
@@ -97,7 +96,6 @@ template <typename ST, int VEC, int CPL>
 __global__ void __launch_bounds__(256) k_batch(BatchArgs ba) {
     const int lane = threadIdx.x & 31;
     const bool odd = ba.step & 1;
-    const prop::Pol pol = prop::make_pol(0);
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(ba.counter, 1ull);
@@ -124,7 +122,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs ba) {
         a.split_count = ba.split_count + gd.split_off;
         a.partials = ba.partials + gd.partial_off;
         a.err = ba.err;
-        dispatch<ST, VEC, CPL>(gd.variant, a, bt.t, lane, pol);
+        dispatch<ST, VEC, CPL>(gd.variant, a, bt.t, lane);
         __syncwarp();
     }
 }

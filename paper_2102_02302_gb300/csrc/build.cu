@@ -208,6 +208,7 @@ void graph_release(cleora_ctx* ctx) {
     dfree_null(ctx, g.val);
     dfree_null(ctx, g.inv_deg);
     dfree_null(ctx, g.deg);
+    dfree_null(ctx, g.hot_cnt);
     g = Graph();
 }
 
@@ -471,6 +472,7 @@ int csr_values_out(cleora_ctx* ctx, float* val_dev) {
     Graph& g = ctx->g;
     if (g.nnz == 0) return CLEORA_OK;
     if (g.has_val) {
+        if (g.hot_cnt) return values_out_sorted(ctx, val_dev);
         CL_CUDA(ctx, cudaMemcpyAsync(val_dev, g.val, g.nnz * sizeof(float), cudaMemcpyDeviceToDevice,
                                      ctx->stream));
         return CLEORA_OK;

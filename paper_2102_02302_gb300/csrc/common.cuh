@@ -38,8 +38,12 @@ struct Graph {
     int64_t n = 0, nnz = 0, max_row_len = 0;
     bool has_val = false;
     bool directed = false;
-    int64_t marked_row_bytes = 0;  // != 0: col bit 31 marks hot rows for this row size
-    int64_t marked_budget = 0;     // ... and this hot-row budget
+    // Rows partitioned hot-first (entries pointing at the hottest rows of T first, each part in
+    // ascending column order): hot_cnt != NULL, for this row size and hot-row budget.
+    int64_t part_row_bytes = 0;
+    int64_t part_budget = 0;
+    int32_t* hot_cnt = nullptr;  // n: hot entries at the front of each row
+    int64_t hot_entries = 0;     // their total
     uint64_t* ids = nullptr;
     int64_t* rowptr = nullptr;
     int32_t* col = nullptr;
@@ -179,6 +183,7 @@ int sort_unique_ids(cleora_ctx* ctx, const uint64_t* keys, int64_t count, uint64
 int rank_ids(cleora_ctx* ctx, const uint64_t* ids, int64_t n, const uint64_t* x, int64_t count,
              int32_t* rank_out);  // rank of each x among ids, -1 when absent
 int csr_values_out(cleora_ctx* ctx, float* val_dev);  // M_ab per entry as FP32
+int values_out_sorted(cleora_ctx* ctx, float* val_dev);  // weighted values, ascending column order
 
 void ctx_release_all(cleora_ctx* ctx);  // graph, plan and embeddings of a context
 
@@ -192,7 +197,8 @@ int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz);
 void plan_release(cleora_ctx* ctx);
 int plan_ensure(cleora_ctx* ctx);
 int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout);
-int hot_mark(cleora_ctx* ctx);                 // mark gathers of hot rows (after init)
-int col_out(cleora_ctx* ctx, int32_t* col_dev); // column indices without the hot bit
+int hot_partition(cleora_ctx* ctx);            // partition rows hot-first (after init)
+int hot_restore(cleora_ctx* ctx);              // back to ascending column order
+int col_out(cleora_ctx* ctx, int32_t* col_dev); // column indices in ascending order per row
 
 }  // namespace cleora

@@ -31,7 +31,6 @@ __global__ void __launch_bounds__(256) k_rows(prop::Args a, int64_t nrows, unsig
     using K = prop::Kern<ST, VEC, CPL, G, HV>;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
-    const prop::Pol pol = prop::make_pol(0);
     const int64_t ntasks = (nrows + ROWS_PER_TASK - 1) / ROWS_PER_TASK;
     for (;;) {
         unsigned long long t = 0;
@@ -39,7 +38,7 @@ __global__ void __launch_bounds__(256) k_rows(prop::Args a, int64_t nrows, unsig
         t = __shfl_sync(prop::FULL, t, 0);
         if ((int64_t)t >= ntasks) break;
         const int64_t rb = (int64_t)t * ROWS_PER_TASK;
-        K::rows_coop(a, rb, min(nrows, rb + ROWS_PER_TASK), lane, g, lg, pol);
+        K::rows_coop(a, rb, min(nrows, rb + ROWS_PER_TASK), lane, g, lg);
         __syncwarp();
     }
 }

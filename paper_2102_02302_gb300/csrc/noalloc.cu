@@ -107,7 +107,6 @@ template <typename ST, int VEC, int CPL, int G, bool HV>
 __global__ void __launch_bounds__(256) k_propagate_noalloc(prop::Args a, unsigned char* scratch) {
     using K = prop::Kern<ST, VEC, CPL, G, HV, true>;  // caller's CSR: check every index
     View v = view_of(scratch);
-    const prop::Pol pol = prop::make_pol(0);
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
     const bool ok_split = v.hdr->overflow == 0;
@@ -126,11 +125,11 @@ __global__ void __launch_bounds__(256) k_propagate_noalloc(prop::Args a, unsigne
             task.b = i;
             task.c = (int32_t)(t - v.split_base[i]);
             task.k = v.split_nch[i];
-            K::split_chunk(a, task, lane, g, lg, pol);
+            K::split_chunk(a, task, lane, g, lg);
         } else {
             const int64_t rb = ((int64_t)t - nchunks) * ROWS_PER_BLOCK;
             const int64_t re = min(a.n, rb + ROWS_PER_BLOCK);
-            K::template rows_coop<true>(a, rb, re, lane, g, lg, pol);
+            K::template rows_coop<true>(a, rb, re, lane, g, lg);
         }
         __syncwarp();
     }

@@ -9,6 +9,7 @@
 // the graph and the two sizes, never on timing, so the summation order of every row is
 // fixed by the graph's shape.
 #include <cub/device/device_scan.cuh>
+#include <cub/device/device_segmented_sort.cuh>
 #include <cub/device/device_select.cuh>
 #include <thrust/iterator/counting_iterator.h>
 
@@ -91,7 +92,7 @@ __device__ __forceinline__ int count_bin(uint32_t c) {
 __global__ void k_indegree(const int32_t* col, int64_t nnz, uint32_t* cnt) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(cnt + (col[k] & 0x7fffffff), 1u);
+        atomicAdd(cnt + col[k], 1u);
 }
 
 __global__ void k_rowlen(const int64_t* rowptr, int64_t n, uint32_t* cnt) {
@@ -118,18 +119,101 @@ __global__ void k_bins(const uint32_t* cnt, int64_t n, uint8_t* bin, unsigned lo
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
-__global__ void k_mark(int32_t* col, int64_t nnz, const uint8_t* bin, int threshold) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = col[k] & 0x7fffffff;
-        col[k] = (bin[c] >= threshold) ? (int32_t)((uint32_t)c | 0x80000000u) : c;
+// Hot flags of 32 consecutive entries as one bit word per thread, and the word's count.
+__global__ void k_hot_words(const int32_t* col, int64_t nnz, const uint8_t* bin, int threshold, uint32_t* word,
+                            int64_t* cnt, int64_t nw) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = w * 32;
+        uint32_t bits = 0;
+        if (k0 + 32 <= nnz) {
+            const int4* p = reinterpret_cast<const int4*>(col + k0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int4 c = __ldcs(p + q);
+                bits |= (uint32_t)(bin[c.x] >= threshold) << (4 * q);
+                bits |= (uint32_t)(bin[c.y] >= threshold) << (4 * q + 1);
+                bits |= (uint32_t)(bin[c.z] >= threshold) << (4 * q + 2);
+                bits |= (uint32_t)(bin[c.w] >= threshold) << (4 * q + 3);
+            }
+        } else {
+            for (int j = 0; k0 + j < nnz; ++j) bits |= (uint32_t)(bin[col[k0 + j]] >= threshold) << j;
+        }
+        word[w] = bits;
+        cnt[w] = __popc(bits);
     }
 }
 
-__global__ void k_unmark_copy(const int32_t* col, int64_t nnz, int32_t* out) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
-         k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = col[k] & 0x7fffffff;
+// Hot entries among positions [0, p) (base: exclusive prefix of the word counts).
+__device__ __forceinline__ int64_t hot_before(const uint32_t* word, const int64_t* base, int64_t nw, int64_t p) {
+    const int64_t w = p >> 5;
+    if (w >= nw) return base[nw - 1] + __popc(word[nw - 1]);
+    return base[w] + __popc(word[w] & ((1u << (p & 31)) - 1u));
+}
+
+// Per row: hot entries before its start (rowH, n + 1 values) and in the row (hot_cnt).
+__global__ void k_row_hot(const int64_t* rowptr, int64_t n, const uint32_t* word, const int64_t* base, int64_t nw,
+                          int64_t* rowH, int32_t* hot_cnt) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t hb = hot_before(word, base, nw, rowptr[r]);
+        const int64_t he = hot_before(word, base, nw, rowptr[r + 1]);
+        rowH[r] = hb;
+        hot_cnt[r] = (int32_t)(he - hb);
+        if (r == n - 1) rowH[n] = he;
+    }
+}
+
+// Last row r in [lo, hi] with rowptr[r] <= k (the row holding entry k; empty rows skipped).
+__device__ __forceinline__ int64_t row_of(const int64_t* rowptr, int64_t k, int64_t lo, int64_t hi) {
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (rowptr[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Stable hot-first partition of every row: thread per 32-entry word, 256 words per block.  A
+// hot entry k of row [beg, end) goes to beg + (hot entries of the row before k); a cold one
+// after the row's hot part, to k - H(k) + H(end), H(p) = hot entries in [0, p).
+__global__ void __launch_bounds__(256) k_hot_scatter(const int64_t* rowptr, int64_t n, const int32_t* col,
+                                                     const float* val, int64_t nnz, const uint32_t* word,
+                                                     const int64_t* base, int64_t nw, const int64_t* rowH,
+                                                     int32_t* col2, float* val2) {
+    __shared__ int64_t s_lo, s_hi;
+    for (int64_t wb = blockIdx.x * 256ll; wb < nw; wb += (int64_t)gridDim.x * 256ll) {
+        if (threadIdx.x == 0) {
+            s_lo = row_of(rowptr, wb * 32, 0, n - 1);
+            s_hi = row_of(rowptr, min(nnz, (wb + 256) * 32) - 1, s_lo, n - 1);
+        }
+        __syncthreads();
+        const int64_t w = wb + threadIdx.x;
+        if (w < nw) {
+            const int64_t k0 = w * 32;
+            const int m = (int)min((int64_t)32, nnz - k0);
+            int64_t r = row_of(rowptr, k0, s_lo, s_hi);
+            int64_t beg = rowptr[r], end = rowptr[r + 1], hb = rowH[r], he = rowH[r + 1];
+            int64_t H = base[w];
+            const uint32_t bits = word[w];
+            for (int j = 0; j < m; ++j) {
+                const int64_t k = k0 + j;
+                while (k >= end) {
+                    ++r;
+                    beg = end;
+                    end = rowptr[r + 1];
+                    hb = he;
+                    he = rowH[r + 1];
+                }
+                const bool hot = (bits >> j) & 1u;
+                const int64_t pos = hot ? beg + (H - hb) : k - H + he;
+                col2[pos] = col[k];
+                if (val) val2[pos] = val[k];
+                H += hot ? 1 : 0;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 int pow2ceil(int v) {
@@ -279,81 +363,182 @@ int plan_ensure(cleora_ctx* ctx) {
     return CLEORA_OK;
 }
 
-// Marks (bit 31 of col) the entries that point at the rows with the largest in-degree, as
-// many rows as fit in the hot-row L2 budget at the current row size.  Gathers of marked rows
-// are issued with an L2 evict_last policy, the others evict_first, so the rows that most
-// entries share stay in L2 while the long tail streams through.  Graphs whose whole T fits
-// twice in the budget are left unmarked (everything is reused anyway).
-int hot_mark(cleora_ctx* ctx) {
+// Entries of every row in ascending column order, from the hot-first layout: a segmented
+// sort of each row's column indices (with their values) into the given buffers.
+static int sort_rows(cleora_ctx* ctx, const int32_t* col, const float* val, int32_t* col_dst, float* val_dst) {
+    const Graph& g = ctx->g;
+    cudaStream_t s = ctx->stream;
+    size_t tb = 0;
+    cudaError_t e = val ? cub::DeviceSegmentedSort::SortPairs(nullptr, tb, col, col_dst, val, val_dst, g.nnz, g.n,
+                                                              g.rowptr, g.rowptr + 1, s)
+                        : cub::DeviceSegmentedSort::SortKeys(nullptr, tb, col, col_dst, g.nnz, g.n, g.rowptr,
+                                                             g.rowptr + 1, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "row sort", __FILE__, __LINE__);
+    void* tmp = nullptr;
+    CL_TRY(dalloc_bytes(ctx, &tmp, tb ? tb : 1));
+    e = val ? cub::DeviceSegmentedSort::SortPairs(tmp, tb, col, col_dst, val, val_dst, g.nnz, g.n, g.rowptr,
+                                                  g.rowptr + 1, s)
+            : cub::DeviceSegmentedSort::SortKeys(tmp, tb, col, col_dst, g.nnz, g.n, g.rowptr, g.rowptr + 1, s);
+    dfree(ctx, tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "row sort", __FILE__, __LINE__);
+    ctx->launches++;
+    return CLEORA_OK;
+}
+
+int hot_restore(cleora_ctx* ctx) {
+    Graph& g = ctx->g;
+    if (!g.hot_cnt) return CLEORA_OK;
+    int32_t* col2 = nullptr;
+    float* val2 = nullptr;
+    CL_TRY(dalloc(ctx, &col2, (size_t)g.nnz));
+    if (g.has_val) {
+        int rc = dalloc(ctx, &val2, (size_t)g.nnz);
+        if (rc) { dfree(ctx, col2); return rc; }
+    }
+    int rc = sort_rows(ctx, g.col, g.has_val ? g.val : nullptr, col2, val2);
+    if (rc) {
+        dfree(ctx, col2);
+        dfree(ctx, val2);
+        return rc;
+    }
+    dfree(ctx, g.col);
+    g.col = col2;
+    if (g.has_val) {
+        dfree(ctx, g.val);
+        g.val = val2;
+    }
+    dfree_null(ctx, g.hot_cnt);
+    g.part_row_bytes = 0;
+    g.part_budget = 0;
+    return CLEORA_OK;
+}
+
+// Partitions every row hot-first: the entries that point at the rows with the largest
+// in-degree (as many rows as fit in the hot-row L2 budget at the current row size) move to
+// the front of the row, both parts keeping ascending column order.  The kernel gathers the
+// hot part with an L2 evict_last policy and the rest evict_first, so the rows that most
+// entries share stay in L2 while the long tail streams through; the policy is uniform over
+// each part, so no entry carries a mark.  Graphs whose whole T fits twice in the budget are
+// left as they are (everything is reused anyway).
+int hot_partition(cleora_ctx* ctx) {
     Graph& g = ctx->g;
     const int64_t row_bytes = (int64_t)ctx->d * (ctx->dtype == CLEORA_F32 ? 4 : 2);
     const int64_t opt = ctx->opt[CLEORA_OPT_HOT_BYTES];
     const int64_t budget = opt == 0 ? DEFAULT_HOT_BYTES : (opt == 1 ? 0 : opt);
-    // BF16 gathers are issued without cache policies (see the kernel's tuning notes)
-    const bool want = ctx->dtype == CLEORA_F32 && budget > 0 && g.n > 0 && g.n * row_bytes > 2 * budget;
-    const int target = want ? 1 : 0;
-    if (!want && g.marked_row_bytes == 0) return CLEORA_OK;
-    if (want && g.marked_row_bytes == row_bytes && g.marked_budget == budget) return CLEORA_OK;
+    const bool uses = ctx->dtype == CLEORA_F32 ? prop::Tune<float>::POLICY : prop::Tune<__nv_bfloat16>::POLICY;
+    const bool want = uses && budget > 0 && g.n > 0 && g.nnz > 0 && g.n * row_bytes > 2 * budget;
+    if (!want && !g.hot_cnt) return CLEORA_OK;
+    if (want && g.hot_cnt && g.part_row_bytes == row_bytes && g.part_budget == budget) return CLEORA_OK;
+    CL_TRY(hot_restore(ctx));
+    if (!want) return CLEORA_OK;
     cudaStream_t s = ctx->stream;
     const int sms = ctx->num_sms;
+    const int64_t nw = (g.nnz + 31) / 32;
     int threshold = 128;  // none hot
     uint32_t* cnt = nullptr;
     uint8_t* bin = nullptr;
     unsigned long long* hist = nullptr;
+    uint32_t* word = nullptr;
+    int64_t* wcnt = nullptr;
+    int64_t* rowH = nullptr;
+    int32_t* hot_cnt = nullptr;
+    int32_t* col2 = nullptr;
+    float* val2 = nullptr;
+    void* tmp = nullptr;
     int rc = CLEORA_OK;
     do {
-        if (target) {
-            if ((rc = dalloc(ctx, &cnt, (size_t)g.n))) break;
-            if ((rc = dalloc(ctx, &bin, (size_t)g.n))) break;
-            if ((rc = dalloc(ctx, &hist, 128))) break;
-            cudaError_t e = cudaMemsetAsync(hist, 0, 128 * sizeof(unsigned long long), s);
-            if (e == cudaSuccess && g.directed) e = cudaMemsetAsync(cnt, 0, g.n * sizeof(uint32_t), s);
-            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot mark", __FILE__, __LINE__); break; }
-            if (g.directed)
-                k_indegree<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, cnt);
-            else  // symmetric: in-degree = row length
-                k_rowlen<<<grid_for(g.n, 256, sms), 256, 0, s>>>(g.rowptr, g.n, cnt);
-            k_bins<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, g.n, bin, hist);
-            ctx->launches += 2;
-            unsigned long long h[128];
-            e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot mark", __FILE__, __LINE__); break; }
-            const int64_t rows = budget / row_bytes;
-            int64_t acc = 0;
-            for (int b = 127; b >= 1; --b) {  // whole bins, from the hottest down
-                if (acc + (int64_t)h[b] > rows) break;
-                acc += (int64_t)h[b];
-                threshold = b;
-            }
-            if (threshold == 128) { rc = CLEORA_OK; }
+        if ((rc = dalloc(ctx, &cnt, (size_t)g.n))) break;
+        if ((rc = dalloc(ctx, &bin, (size_t)g.n))) break;
+        if ((rc = dalloc(ctx, &hist, 128))) break;
+        cudaError_t e = cudaMemsetAsync(hist, 0, 128 * sizeof(unsigned long long), s);
+        if (e == cudaSuccess && g.directed) e = cudaMemsetAsync(cnt, 0, g.n * sizeof(uint32_t), s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
+        if (g.directed)
+            k_indegree<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, cnt);
+        else  // symmetric: in-degree = row length
+            k_rowlen<<<grid_for(g.n, 256, sms), 256, 0, s>>>(g.rowptr, g.n, cnt);
+        k_bins<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, g.n, bin, hist);
+        ctx->launches += 2;
+        unsigned long long h[128];
+        e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
+        const int64_t rows = budget / row_bytes;
+        int64_t acc = 0;
+        for (int b = 127; b >= 1; --b) {  // whole bins, from the hottest down
+            if (acc + (int64_t)h[b] > rows) break;
+            acc += (int64_t)h[b];
+            threshold = b;
         }
-        if (target && threshold < 128) {
-            k_mark<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, threshold);
-            ctx->launches++;
-            g.marked_row_bytes = row_bytes;
-            g.marked_budget = budget;
-        } else if (g.marked_row_bytes != 0) {
-            k_unmark_copy<<<grid_for(g.nnz, 256, sms), 256, 0, s>>>(g.col, g.nnz, g.col);
-            ctx->launches++;
-            g.marked_row_bytes = 0;
-            g.marked_budget = 0;
+        if (threshold == 128) break;  // no whole bin fits: leave the rows as they are
+        dfree_null(ctx, cnt);
+        if ((rc = dalloc(ctx, &word, (size_t)nw))) break;
+        if ((rc = dalloc(ctx, &wcnt, (size_t)nw))) break;
+        if ((rc = dalloc(ctx, &rowH, (size_t)(g.n + 1)))) break;
+        if ((rc = dalloc(ctx, &hot_cnt, (size_t)g.n))) break;
+        if ((rc = dalloc(ctx, &col2, (size_t)g.nnz))) break;
+        if (g.has_val && (rc = dalloc(ctx, &val2, (size_t)g.nnz))) break;
+        k_hot_words<<<grid_for(nw, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, threshold, word, wcnt, nw);
+        ctx->launches++;
+        size_t tb = 0;
+        e = cub::DeviceScan::ExclusiveSum(nullptr, tb, wcnt, wcnt, nw, s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
+        if ((rc = dalloc_bytes(ctx, &tmp, tb ? tb : 1))) break;
+        e = cub::DeviceScan::ExclusiveSum(tmp, tb, wcnt, wcnt, nw, s);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
+        ctx->launches++;
+        k_row_hot<<<grid_for(g.n, 256, sms), 256, 0, s>>>(g.rowptr, g.n, word, wcnt, nw, rowH, hot_cnt);
+        const int64_t blocks = std::min<int64_t>((nw + 255) / 256, (int64_t)sms * 8);
+        k_hot_scatter<<<(unsigned)blocks, 256, 0, s>>>(g.rowptr, g.n, g.col, g.has_val ? g.val : nullptr, g.nnz,
+                                                       word, wcnt, nw, rowH, col2, val2);
+        ctx->launches += 2;
+        int64_t hot_total = 0;
+        e = cudaMemcpyAsync(&hot_total, rowH + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
+        g.hot_entries = hot_total;
+        dfree(ctx, g.col);
+        g.col = col2;
+        col2 = nullptr;
+        if (g.has_val) {
+            dfree(ctx, g.val);
+            g.val = val2;
+            val2 = nullptr;
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "hot mark", __FILE__, __LINE__);
+        g.hot_cnt = hot_cnt;
+        hot_cnt = nullptr;
+        g.part_row_bytes = row_bytes;
+        g.part_budget = budget;
     } while (0);
     dfree(ctx, cnt);
     dfree(ctx, bin);
     dfree(ctx, hist);
+    dfree(ctx, word);
+    dfree(ctx, wcnt);
+    dfree(ctx, rowH);
+    dfree(ctx, hot_cnt);
+    dfree(ctx, col2);
+    dfree(ctx, val2);
+    dfree(ctx, tmp);
     return rc;
 }
 
 int col_out(cleora_ctx* ctx, int32_t* col_dev) {
     const Graph& g = ctx->g;
     if (g.nnz == 0) return CLEORA_OK;
-    k_unmark_copy<<<grid_for(g.nnz, 256, ctx->num_sms), 256, 0, ctx->stream>>>(g.col, g.nnz, col_dev);
-    CL_LAUNCHED(ctx);
+    if (g.hot_cnt) return sort_rows(ctx, g.col, nullptr, col_dev, nullptr);
+    CL_CUDA(ctx, cudaMemcpyAsync(col_dev, g.col, g.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
     return CLEORA_OK;
+}
+
+int values_out_sorted(cleora_ctx* ctx, float* val_dev) {
+    const Graph& g = ctx->g;
+    int32_t* keys = nullptr;
+    CL_TRY(dalloc(ctx, &keys, (size_t)g.nnz));
+    const int rc = sort_rows(ctx, g.col, g.val, keys, val_dev);
+    dfree(ctx, keys);
+    return rc;
 }
 
 int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
@@ -380,7 +565,7 @@ int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
     a.split_count = p.split_count;
     a.partials = p.partials;
     a.err = ctx->err_flag;
-    a.hints = g.marked_row_bytes != 0 ? 1 : 0;
+    a.hot_cnt = g.hot_cnt;
     CL_CUDA(ctx, cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), ctx->stream));
     const int bps = (int)ctx->opt[CLEORA_OPT_BLOCKS_PER_SM];
     cudaError_t e;

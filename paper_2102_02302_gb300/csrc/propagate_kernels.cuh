@@ -24,13 +24,13 @@
 
 // Compile-time tuning knobs, chosen per storage type from measurements on GB300 (the
 // 1.4B-edge power-law graph, d = 128):
-//   FP32: hot/cold L2 policies on the gathers (-15% time), one batch path, >= 4 CTAs/SM;
-//   BF16: plain gathers (the 64-bit policy registers cost more than they save), a separate
-//         full-batch path, >= 4 CTAs/SM.
+//   FP32: one batch path, scalar FP32 adds, >= 4 CTAs/SM;
+//   BF16: a separate full-batch path, paired FP32 adds (-3.5% time), >= 4 CTAs/SM;
+//   both: 8 gathered vectors in flight per lane, and L2 policies on the gathers of
+//   partitioned rows (hot segment evict_last, cold segment evict_first).  Rows are
+//   partitioned only for graphs whose T is much larger than the hot-row budget; the policy of
+//   a segment is uniform, so it costs no per-entry work.
 // A -D on the command line overrides the choice for both types (experiments).
-#ifndef CLEORA_INFLIGHT
-#define CLEORA_INFLIGHT 8      // gathered vectors in flight per lane and batch
-#endif
 #ifndef CLEORA_COLD_POLICY
 #define CLEORA_COLD_POLICY 0   // gathers of unmarked rows: 0 evict_first, 1 evict_normal
 #endif
@@ -60,37 +60,38 @@ struct Args {
     int32_t* split_count;
     float* partials;
     int* err;
-    int hints = 0;  // 1: column entries with bit 31 set point at hot rows (keep them in L2)
+    // Rows partitioned hot-first: the first hot_cnt[r] entries of row r point at rows kept in
+    // L2 (gathered evict_last), the rest (in descending column order) are gathered
+    // evict_first.  NULL: no partition, every gather evict_normal.
+    const int32_t* hot_cnt = nullptr;
 };
 
-// L2 policies of the gathers: rows marked hot are loaded evict_last, the rest evict_first
-// (with hints off both are evict_normal).
-struct Pol {
-    uint64_t hot, cold;
-};
-
-__device__ __forceinline__ Pol make_pol(int hints) {
-    Pol p;
-    if (hints) {
-        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.hot));
+// L2 policy of a gather: in a partitioned row the hot segment is loaded evict_last and the
+// cold one evict_first; without a partition every gather is evict_normal.  Made where it is
+// used (one instruction) rather than held in registers across the row loops.
+__device__ __forceinline__ uint64_t seg_policy(bool partitioned, bool hot) {
+    uint64_t p;
+    if (!partitioned)
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    else if (hot)
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else
 #if CLEORA_COLD_POLICY == 0
-        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.cold));
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
 #else
-        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p.cold));
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
 #endif
-    } else {
-        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p.hot));
-        p.cold = p.hot;
-    }
     return p;
 }
 
 template <typename ST> struct Tune;
+// POLICY: gathers carry the L2 policy of their row segment (hot / cold); otherwise they are
+// plain loads and the partition only changes the summation order.
 template <> struct Tune<float> {
-#ifdef CLEORA_GATHER_HINTS
-    static constexpr bool HINTS = CLEORA_GATHER_HINTS;
+#ifdef CLEORA_POLICY_F32
+    static constexpr bool POLICY = CLEORA_POLICY_F32;
 #else
-    static constexpr bool HINTS = true;
+    static constexpr bool POLICY = true;
 #endif
 #ifdef CLEORA_FULL_BATCH
     static constexpr bool FULLB = CLEORA_FULL_BATCH;
@@ -102,12 +103,22 @@ template <> struct Tune<float> {
 #else
     static constexpr int MINB = 4;
 #endif
+#ifdef CLEORA_INFLIGHT_F32
+    static constexpr int INFLIGHT = CLEORA_INFLIGHT_F32;
+#else
+    static constexpr int INFLIGHT = 8;  // gathered vectors in flight per lane and batch
+#endif
+#ifdef CLEORA_PACKED_F32
+    static constexpr bool PACKED = CLEORA_PACKED_F32;
+#else
+    static constexpr bool PACKED = false;  // paired FP32 adds (add/fma .f32x2)
+#endif
 };
 template <> struct Tune<__nv_bfloat16> {
-#ifdef CLEORA_GATHER_HINTS
-    static constexpr bool HINTS = CLEORA_GATHER_HINTS;
+#ifdef CLEORA_POLICY_BF16
+    static constexpr bool POLICY = CLEORA_POLICY_BF16;
 #else
-    static constexpr bool HINTS = false;
+    static constexpr bool POLICY = true;
 #endif
 #ifdef CLEORA_FULL_BATCH
     static constexpr bool FULLB = CLEORA_FULL_BATCH;
@@ -118,6 +129,16 @@ template <> struct Tune<__nv_bfloat16> {
     static constexpr int MINB = CLEORA_MIN_BLOCKS;
 #else
     static constexpr int MINB = 4;
+#endif
+#ifdef CLEORA_INFLIGHT_BF16
+    static constexpr int INFLIGHT = CLEORA_INFLIGHT_BF16;
+#else
+    static constexpr int INFLIGHT = 8;
+#endif
+#ifdef CLEORA_PACKED_BF16
+    static constexpr bool PACKED = CLEORA_PACKED_BF16;
+#else
+    static constexpr bool PACKED = true;
 #endif
 };
 
@@ -162,6 +183,36 @@ __device__ __forceinline__ void set_word(uint2& v, int i, uint32_t w) {
     if (i == 0) v.x = w; else v.y = w;
 }
 
+// a += x and a += w * x on two FP32 lanes at once (Blackwell's paired FP32 pipe:
+// add/fma .f32x2, round-to-nearest like the scalar FADD/FFMA, so results are identical).
+template <bool PACKED>
+__device__ __forceinline__ void add2(float& a0, float& a1, float x0, float x1) {
+    if (PACKED) {
+        uint64_t a, x;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+        asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(x));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(a));
+    } else {
+        a0 += x0;
+        a1 += x1;
+    }
+}
+template <bool PACKED>
+__device__ __forceinline__ void fma2(float& a0, float& a1, float w, float x0, float x1) {
+    if (PACKED) {
+        uint64_t a, x, ww;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+        asm("mov.b64 %0, {%1, %1};" : "=l"(ww) : "f"(w));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a) : "l"(ww), "l"(x));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(a));
+    } else {
+        a0 = fmaf(w, x0, a0);
+        a1 = fmaf(w, x1, a1);
+    }
+}
+
 // Element traits: FP32 has one element per 32-bit word, BF16 two.
 template <typename ST> struct EL;
 template <> struct EL<float> {
@@ -182,14 +233,14 @@ template <> struct EL<__nv_bfloat16> {
 };
 
 // CHECK: verify every column index against n (a CSR that does not come from this library's
-// own build); otherwise the index is trusted and only its hot bit is stripped.
+// own build); otherwise the index is trusted.
 template <typename ST, int VEC, int CPL, int G, bool HV, bool CHECK = false>
 struct Kern {
     using VT = typename VecT<VEC>::T;
     static constexpr int W = VEC / 4;                       // 32-bit words per vector
     static constexpr int EPV = W * EL<ST>::PER_WORD;        // elements per vector
     static constexpr int P = 32 / G;                        // lane groups per warp
-    static constexpr int U = CPL >= CLEORA_INFLIGHT ? 1 : CLEORA_INFLIGHT / CPL;  // entries per batch
+    static constexpr int U = CPL >= Tune<ST>::INFLIGHT ? 1 : Tune<ST>::INFLIGHT / CPL;  // entries per batch
 
     // Two-level sum: `v` collects at most one 32-entry window, then is added into `t`.  Every
     // serial FP32 chain stays short (window + windows-per-row) even for a row of thousands of
@@ -207,23 +258,21 @@ struct Kern {
 #pragma unroll
             for (int i = 0; i < CPL; ++i)
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) {
-                    t[i][e] += v[i][e];
-                    v[i][e] = 0.f;
+                for (int e = 0; e < EPV; e += 2) {
+                    add2<Tune<ST>::PACKED>(t[i][e], t[i][e + 1], v[i][e], v[i][e + 1]);
+                    v[i][e] = v[i][e + 1] = 0.f;
                 }
         }
     };
 
     __device__ static __forceinline__ void add_vec(Acc& acc, int i, const VT& x, float w) {
+        float f[EPV];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            float f[EL<ST>::PER_WORD];
-            EL<ST>::unpack(word(x, k), f);
+        for (int k = 0; k < W; ++k) EL<ST>::unpack(word(x, k), f + k * EL<ST>::PER_WORD);
 #pragma unroll
-            for (int h = 0; h < EL<ST>::PER_WORD; ++h) {
-                if (HV) acc.v[i][k * EL<ST>::PER_WORD + h] = fmaf(w, f[h], acc.v[i][k * EL<ST>::PER_WORD + h]);
-                else acc.v[i][k * EL<ST>::PER_WORD + h] += f[h];
-            }
+        for (int e = 0; e < EPV; e += 2) {
+            if (HV) fma2<Tune<ST>::PACKED>(acc.v[i][e], acc.v[i][e + 1], w, f[e], f[e + 1]);
+            else add2<Tune<ST>::PACKED>(acc.v[i][e], acc.v[i][e + 1], f[e], f[e + 1]);
         }
     }
 
@@ -237,86 +286,83 @@ struct Kern {
     // Entries j = j0 + u*P + g (u < U) of a window of column indices held one per lane
     // (`mc`, `mw`), restricted to j < jh; all 32 lanes execute the shuffles.  FULLB: every
     // entry of the batch is valid, so no entry needs a validity test.  Invalid entries load
-    // nothing and add a zero vector (this form also keeps register use lowest).
+    // nothing and add a zero vector (this form also keeps register use lowest).  `cp` is the
+    // L2 policy of the whole segment.
     template <bool FULLB>
     __device__ static __forceinline__ void gather_batch(const Args& a, Acc& acc, int mc, float mw,
-                                                        int j0, int jh, int g, int lg, const Pol& pol) {
+                                                        int j0, int jh, int g, int lg, uint64_t cp) {
         VT x[U][CPL];
         float w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u * P + g;
-            const int raw = __shfl_sync(FULL, mc, j & 31);
+            const int c = __shfl_sync(FULL, mc, j & 31);
             const float wu = HV ? __shfl_sync(FULL, mw, j & 31) : 1.f;
             bool ok = FULLB || j < jh;
-            const int c = raw & 0x7fffffff;
-            if (CHECK && ok && c >= a.n) {  // corrupt index: flag, skip
+            if (CHECK && ok && (unsigned)c >= (unsigned)a.n) {  // corrupt index: flag, skip
                 atomicOr(a.err, 1);
                 ok = false;
             }
             w[u] = ok ? wu : 0.f;
             const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * a.row_bytes) + lg;
-            const uint64_t cp = raw < 0 ? pol.hot : pol.cold;
 #pragma unroll
-            for (int i = 0; i < CPL; ++i)
-                if (Tune<ST>::HINTS)
+            for (int i = 0; i < CPL; ++i) {
+                if (Tune<ST>::POLICY)
                     x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G, cp) : zero_vec();
                 else
                     x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G) : zero_vec();
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int i = 0; i < CPL; ++i)
-                add_vec(acc, i, x[u][i], w[u]);
+            for (int i = 0; i < CPL; ++i) add_vec(acc, i, x[u][i], w[u]);
     }
 
     // Same for one lane group working alone (mode 2): window of G entries, entries j0+u.
     template <bool FULLB>
     __device__ static __forceinline__ void gather_batch_group(const Args& a, Acc& acc, int mc, float mw,
                                                               int j0, int jh, int lg, unsigned gmask,
-                                                              const Pol& pol) {
+                                                              uint64_t cp) {
         VT x[U][CPL];
         float w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u;
-            const int raw = __shfl_sync(gmask, mc, j & (G - 1), G);
+            const int c = __shfl_sync(gmask, mc, j & (G - 1), G);
             const float wu = HV ? __shfl_sync(gmask, mw, j & (G - 1), G) : 1.f;
             bool ok = FULLB || j < jh;
-            const int c = raw & 0x7fffffff;
-            if (CHECK && ok && c >= a.n) {
+            if (CHECK && ok && (unsigned)c >= (unsigned)a.n) {
                 atomicOr(a.err, 1);
                 ok = false;
             }
             w[u] = ok ? wu : 0.f;
             const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * a.row_bytes) + lg;
-            const uint64_t cp = raw < 0 ? pol.hot : pol.cold;
 #pragma unroll
-            for (int i = 0; i < CPL; ++i)
-                if (Tune<ST>::HINTS)
+            for (int i = 0; i < CPL; ++i) {
+                if (Tune<ST>::POLICY)
                     x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G, cp) : zero_vec();
                 else
                     x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G) : zero_vec();
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int i = 0; i < CPL; ++i)
-                add_vec(acc, i, x[u][i], w[u]);
+            for (int i = 0; i < CPL; ++i) add_vec(acc, i, x[u][i], w[u]);
     }
 
-    // Entries [jl, jh) of the current window, full batches without predicates.
+    // Entries [jl, jh) of the current window under one policy.
     __device__ static __forceinline__ void gather_window(const Args& a, Acc& acc, int mc, float mw, int jl,
-                                                         int jh, int g, int lg, const Pol& pol) {
+                                                         int jh, int g, int lg, uint64_t cp) {
         int j0 = jl;
         if (Tune<ST>::FULLB) {
 #pragma unroll 1
-            for (; j0 + P * U <= jh; j0 += P * U) gather_batch<true>(a, acc, mc, mw, j0, jh, g, lg, pol);
-            if (j0 < jh) gather_batch<false>(a, acc, mc, mw, j0, jh, g, lg, pol);
+            for (; j0 + P * U <= jh; j0 += P * U) gather_batch<true>(a, acc, mc, mw, j0, jh, g, lg, cp);
+            if (j0 < jh) gather_batch<false>(a, acc, mc, mw, j0, jh, g, lg, cp);
         } else {
 #pragma unroll 1
-            for (; j0 < jh; j0 += P * U) gather_batch<false>(a, acc, mc, mw, j0, jh, g, lg, pol);
+            for (; j0 < jh; j0 += P * U) gather_batch<false>(a, acc, mc, mw, j0, jh, g, lg, cp);
         }
     }
 
@@ -384,17 +430,29 @@ struct Kern {
 
     // Accumulate entries [k0, k1) with the whole warp (groups interleave entries).
     __device__ static __forceinline__ void range_coop(const Args& a, Acc& acc, int64_t k0, int64_t k1,
-                                                      int lane, int g, int lg, const Pol& pol) {
-        for (int64_t cb = k0; cb < k1; cb += 32) {
-            const int jh = (int)min((int64_t)32, k1 - cb);
-            int mc = 0;
-            float mw = 0.f;
-            if (lane < jh) {
-                mc = __ldcs(a.col + cb + lane);
-                if (HV) mw = __ldcs(a.val + cb + lane);
+                                                      int64_t hot_end, int lane, int g, int lg) {
+        const bool part = a.hot_cnt != nullptr;
+        int64_t cb = -64;
+        int mc = 0;
+        float mw = 0.f;
+        for (int64_t k = k0; k < k1;) {
+            if (k >= cb + 32) {
+                cb = k;
+                const int m = (int)min((int64_t)32, k1 - cb);
+                mc = 0;
+                mw = 0.f;
+                if (lane < m) {
+                    mc = __ldcs(a.col + cb + lane);
+                    if (HV) mw = __ldcs(a.val + cb + lane);
+                }
             }
-            gather_window(a, acc, mc, mw, 0, jh, g, lg, pol);
+            // a segment ends at the window's end, the range's end or the row's hot boundary
+            const bool hot = k < hot_end;
+            const int64_t stop = hot ? min(k1, hot_end) : k1;
+            const int jh = (int)min((int64_t)32, stop - cb);
+            gather_window(a, acc, mc, mw, (int)(k - cb), jh, g, lg, seg_policy(part, hot));
             acc.flush();
+            k = cb + jh;
         }
     }
 
@@ -402,8 +460,7 @@ struct Kern {
     // loaded 32 at a time and reused across consecutive rows.  SKIP: leave out rows longer
     // than a.skip_len (a caller that runs those rows as split chunks).
     template <bool SKIP = false>
-    __device__ static void rows_coop(const Args& a, int64_t rb, int64_t re, int lane, int g, int lg,
-                                     const Pol& pol) {
+    __device__ static void rows_coop(const Args& a, int64_t rb, int64_t re, int lane, int g, int lg) {
         int64_t wr = rb, lo = 0, hi = 0;
         if (wr + lane < re) {
             lo = a.rowptr[wr + lane];
@@ -423,6 +480,9 @@ struct Kern {
             }
             const int64_t beg = __shfl_sync(FULL, lo, (int)(r - wr));
             const int64_t end = __shfl_sync(FULL, hi, (int)(r - wr));
+            // hot count: one broadcast load per row (a lane register holding 32 rows' counts,
+            // like rowptr, costs the register that keeps the FP32 kernel from spilling)
+            const int64_t hot_end = beg + (a.hot_cnt ? a.hot_cnt[r] : 0);
             if (SKIP && end - beg > a.skip_len) continue;
             Acc acc;
             acc.zero();
@@ -439,9 +499,11 @@ struct Kern {
                         if (HV) mw = __ldcs(a.val + cb + lane);
                     }
                 }
-                const int jl = (int)(k - cb);
-                const int jh = (int)min((int64_t)32, end - cb);
-                gather_window(a, acc, mc, mw, jl, jh, g, lg, pol);
+                // a segment ends at the window's end, the row's end or its hot boundary
+                const bool hot = k < hot_end;
+                const int64_t stop = hot ? min(end, hot_end) : end;
+                const int jh = (int)min((int64_t)32, stop - cb);
+                gather_window(a, acc, mc, mw, (int)(k - cb), jh, g, lg, seg_policy(a.hot_cnt != nullptr, hot));
                 acc.flush();
                 k = cb + jh;
             }
@@ -451,10 +513,11 @@ struct Kern {
     }
 
     // Mode 2: lane group g owns rows rb + g, rb + g + P, ...
-    __device__ static void rows_group(const Args& a, int64_t rb, int64_t re, int g, int lg, const Pol& pol) {
+    __device__ static void rows_group(const Args& a, int64_t rb, int64_t re, int g, int lg) {
         const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (g * G));
         for (int64_t r = rb + g; r < re; r += P) {
             const int64_t beg = a.rowptr[r], end = a.rowptr[r + 1];
+            const int64_t hot_end = beg + (a.hot_cnt ? a.hot_cnt[r] : 0);
             Acc acc;
             acc.zero();
             if (beg == end) load_own(a, acc, r, lg);
@@ -466,10 +529,17 @@ struct Kern {
                     mc = __ldcs(a.col + cb + lg);
                     if (HV) mw = __ldcs(a.val + cb + lg);
                 }
-                int j0 = 0;
+                const int hj = (int)max((int64_t)0, min((int64_t)jh, hot_end - cb));
 #pragma unroll 1
-                for (; j0 + U <= jh; j0 += U) gather_batch_group<true>(a, acc, mc, mw, j0, jh, lg, gmask, pol);
-                if (j0 < jh) gather_batch_group<false>(a, acc, mc, mw, j0, jh, lg, gmask, pol);
+                for (int part = 0; part < 2; ++part) {
+                    const int pb = part == 0 ? 0 : hj, pe = part == 0 ? hj : jh;
+                    const uint64_t cp = seg_policy(a.hot_cnt != nullptr, part == 0);
+                    int j0 = pb;
+#pragma unroll 1
+                    for (; j0 + U <= pe; j0 += U)
+                        gather_batch_group<true>(a, acc, mc, mw, j0, pe, lg, gmask, cp);
+                    if (j0 < pe) gather_batch_group<false>(a, acc, mc, mw, j0, pe, lg, gmask, cp);
+                }
                 acc.flush();
             }
             finish_row(a, acc, r, lg, true, gmask);
@@ -477,14 +547,14 @@ struct Kern {
     }
 
     // One chunk of a split row; the last chunk to finish combines all partial slots.
-    __device__ static void split_chunk(const Args& a, const Task& t, int lane, int g, int lg, const Pol& pol) {
+    __device__ static void split_chunk(const Args& a, const Task& t, int lane, int g, int lg) {
         const int64_t r = t.a;
         const int64_t beg = a.rowptr[r], end = a.rowptr[r + 1];
         const int64_t k0 = beg + (int64_t)t.c * a.split_len;
         const int64_t k1 = min(end, k0 + a.split_len);
         Acc acc;
         acc.zero();
-        range_coop(a, acc, k0, k1, lane, g, lg, pol);
+        range_coop(a, acc, k0, k1, beg + (a.hot_cnt ? a.hot_cnt[r] : 0), lane, g, lg);
         reduce_groups(acc);
         const int64_t base = a.split_base[t.b];
         float* slot = a.partials + (base + t.c) * (int64_t)a.d;
@@ -532,7 +602,6 @@ k_propagate(Args a) {
     using K = Kern<ST, VEC, CPL, G, HV>;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
-    const Pol pol = make_pol(a.hints);
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1ull);
@@ -540,11 +609,11 @@ k_propagate(Args a) {
         if (t >= (unsigned long long)a.ntasks) break;
         const Task task = a.tasks[t];
         if (task.c >= 0) {
-            K::split_chunk(a, task, lane, g, lg, pol);
+            K::split_chunk(a, task, lane, g, lg);
         } else if (MODE == 1 || G == 32) {
-            K::rows_coop(a, task.a, task.b, lane, g, lg, pol);
+            K::rows_coop(a, task.a, task.b, lane, g, lg);
         } else {
-            K::rows_group(a, task.a, task.b, g, lg, pol);
+            K::rows_group(a, task.a, task.b, g, lg);
         }
         __syncwarp();
     }

@@ -179,7 +179,12 @@ int64_t cleora_serve_estimate(const cleora_job* j) {
     const int64_t plan = resident + n * 53 + (m / 64 + 1) * 16;
     const int64_t prop = resident + (m / 64 + 1) * 16 + 2 * n * j->d * es +
                          (2 * m / 8192 + 1) * j->d * 4 + (es == 2 ? 256 * MiB : 0) + 64 * MiB;
-    const int64_t peak = std::max(build, std::max(plan, prop));
+    // init with T larger than twice the hot-row budget partitions the rows hot-first: a new
+    // column (and value) array, flag words and their counts, bins, row prefixes, hot counts
+    const int64_t part = n * j->d * es > 2 * DEFAULT_HOT_BYTES
+                             ? prop + m * (4 + 4 * w) + m / 8 + m / 4 + n * (5 + 8 + 4) + 64 * MiB
+                             : 0;
+    const int64_t peak = std::max(std::max(build, part), std::max(plan, prop));
     return peak + peak / 10;  // pool rounding and fragmentation
 }
 
