@@ -308,18 +308,37 @@ def e2e_measure(pkg, spec, host_edges, storage, steps, device):
         ctx.graph_build(src_h, dst_h, w_h, spec.directed)
         n = ctx.info()["n"]
         out = torch.empty((n, spec.d), dtype=torch.float32, pin_memory=True)
-        times = []
+        times, phases = [], []
         for s in range(steps + 1):  # first one warms the pool
             t = time.perf_counter()
             ctx.graph_build(src_h, dst_h, w_h, spec.directed)
+            t1 = time.perf_counter()
             ctx.init(spec.d, 0, storage)
+            ctx.sync()
+            t2 = time.perf_counter()
             ctx.propagate(spec.iters, out)
             ctx.sync()
+            t3 = time.perf_counter()
             if s > 0:
-                times.append(time.perf_counter() - t)
+                times.append(t3 - t)
+                phases.append((t1 - t, t2 - t1, t3 - t2))
     h2d = src_h.numel() * 8 * 2 + (0 if w_h is None else w_h.numel() * 4)
     d2h = n * spec.d * 4
-    return float(np.median(times)), h2d, d2h
+    # the host link alone: the same edge upload as plain copies into device tensors
+    dsrc = torch.empty_like(src_h, device=f"cuda:{device}")
+    ddst = torch.empty_like(dst_h, device=f"cuda:{device}")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    dsrc.copy_(src_h, non_blocking=True)
+    ddst.copy_(dst_h, non_blocking=True)
+    torch.cuda.synchronize()
+    t_link = time.perf_counter() - t
+    del dsrc, ddst
+    torch.cuda.empty_cache()
+    ph = np.median(np.array(phases), axis=0)
+    split = {"upload_build_s": float(ph[0]), "init_s": float(ph[1]), "iterate_download_s": float(ph[2]),
+             "edge_copy_only_s": t_link}
+    return float(np.median(times)), h2d, d2h, split
 
 
 # ---------------------------------------------------------------------------------------
@@ -670,14 +689,20 @@ def main():
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        src_h = edges[0].cpu().pin_memory()
-        dst_h = edges[1].cpu().pin_memory()
-        w_h = None if edges[2] is None else edges[2].cpu().pin_memory()
+        def pinned_copy(t):  # a pinned host buffer filled straight from the device tensor
+            if t is None:
+                return None
+            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            h.copy_(t)
+            return h
+
+        src_h, dst_h, w_h = (pinned_copy(t) for t in edges[:3])
         del edges
         torch.cuda.empty_cache()
-        t_e2e, h2d, d2h = e2e_measure(pkg, spec, (src_h, dst_h, w_h), head, args.e2e_steps, device)
+        t_e2e, h2d, d2h, split = e2e_measure(pkg, spec, (src_h, dst_h, w_h), head, args.e2e_steps, device)
         e2e = {"value": world * nnz * d * spec.iters / t_e2e, "unit": "nnz*d/s per iteration",
                "s_per_step": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "phases": split,
                "note": "public C ABI with pinned host buffers: edge upload, build, init, "
                        f"{spec.iters} iterations and FP32 result download per step"}
 

@@ -87,12 +87,29 @@ int check_err_flag(cleora_ctx* ctx) {
 
 // Current embeddings -> `out` as `dtype` (device or host); host copies go through a
 // bounded staging buffer when a conversion is needed.
+// Device address of pinned host memory registered with CUDA (mapped into the device's
+// address space), or NULL for pageable memory.
+void* host_mapped(void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int export_T(cleora_ctx* ctx, void* out, cleora_dtype dtype, int out_on_device) {
     const int64_t count = ctx->g.n * (int64_t)ctx->d;
     if (count == 0) return CLEORA_OK;
     const void* src = ctx->T[ctx->cur];
     if (dtype == ctx->dtype) return copy_out(ctx, out, src, count * elem_size(dtype), out_on_device);
     if (out_on_device) return convert_impl(ctx, src, ctx->dtype, out, dtype, count);
+    void* mapped = host_mapped(out);
+    if (mapped) {  // pinned host memory: convert straight into it over the host link
+        CL_TRY(convert_impl(ctx, src, ctx->dtype, mapped, dtype, count));
+        CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return CLEORA_OK;
+    }
     const int64_t slice = (int64_t)1 << 26;  // elements per staging slice
     void* stage = nullptr;
     CL_TRY(dalloc_bytes(ctx, &stage, (size_t)std::min(count, slice) * elem_size(dtype)));
@@ -116,6 +133,12 @@ int import_T(cleora_ctx* ctx, const void* in, cleora_dtype dtype, int in_on_devi
     if (in_on_device) return convert_impl(ctx, in, dtype, dst, ctx->dtype, count);
     if (dtype == ctx->dtype) {
         CL_CUDA(ctx, cudaMemcpyAsync(dst, in, count * elem_size(dtype), cudaMemcpyHostToDevice, ctx->stream));
+        CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return CLEORA_OK;
+    }
+    void* mapped = host_mapped(const_cast<void*>(in));
+    if (mapped) {  // pinned host memory: convert straight out of it over the host link
+        CL_TRY(convert_impl(ctx, mapped, dtype, dst, ctx->dtype, count));
         CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         return CLEORA_OK;
     }

@@ -3,13 +3,19 @@
 // edges a->b or the sum of their weights; Sec. 4.5: undirected edges count both ways).
 //
 // Steps (all on the context's stream; sort, unique and compaction use CUB):
-//   1. ids   = sort-unique(src ++ dst)                 (node index = rank of the id)
+//   1. ids   = sorted distinct values of src ++ dst   (node index = rank of the id): a hash
+//      set drops the repeats (a power-law edge list names each hub millions of times), and
+//      only the distinct ids are sorted; a second hash table maps each id to its rank
 //   2. entry keys (a << bits) | b, one per edge (two for an undirected non-loop edge,
 //      interleaved 2e, 2e+1 so that a stable sort keeps duplicates in edge order)
 //   3. stable radix sort of the keys (weights carried along when weighted)
 //   4. runs of equal keys -> col, e_ab (count, or FP64 sum in edge order)
 //   5. rowptr from the sorted rows; deg_a = FP64 sum of e_ab in ascending col
 //   6. val = fp32(e_ab / deg_a) when needed; inv_deg = 1.0f / fp32(deg_a)
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_select.cuh>
 #include <thrust/iterator/counting_iterator.h>
@@ -52,23 +58,179 @@ __device__ __forceinline__ int64_t rank_of(const uint64_t* ids, int64_t n, const
     return a;
 }
 
-__global__ void k_entries(const uint64_t* src, const uint64_t* dst, const float* w, int64_t E,
-                          int directed, const uint64_t* ids, int64_t n, const uint64_t* sample,
-                          int64_t ns, int bits, uint64_t invalid, uint64_t* keys, float* vals) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t a = (uint64_t)rank_of(ids, n, sample, ns, src[e]);
-        const uint64_t b = (uint64_t)rank_of(ids, n, sample, ns, dst[e]);
-        if (directed) {
-            keys[e] = (a << bits) | b;
-            if (vals) vals[e] = w[e];
-        } else {
-            keys[2 * e] = (a << bits) | b;
-            keys[2 * e + 1] = (a == b) ? invalid : ((b << bits) | a);
-            if (vals) {
-                vals[2 * e] = w[e];
-                vals[2 * e + 1] = w[e];
+// Hash tables of ids.  The all-ones id is the empty-slot marker: it is never stored, and an
+// edge list that contains it sets a flag instead (it sorts last, so its rank is n - 1).
+constexpr uint64_t EMPTY_ID = ~0ull;
+
+// HyperLogLog sketch of the distinct endpoints (Flajolet, Fusy, Gandouet and Meunier 2007),
+// 2^HLL_P registers: register j keeps the largest rank (position of the first one bit) of
+// the hashes whose top HLL_P bits are j.  It sizes the id set below.
+constexpr int HLL_P = 12;
+constexpr int HLL_M = 1 << HLL_P;
+
+__global__ void k_hll(const uint64_t* src, const uint64_t* dst, int64_t E, unsigned int* regs) {
+    __shared__ unsigned int r[HLL_M];
+    for (int j = threadIdx.x; j < HLL_M; j += blockDim.x) r[j] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * E;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t h = mix64((i < E ? src[i] : dst[i - E]) ^ 0x6A09E667F3BCC909ull);
+        const uint64_t rest = h << HLL_P;
+        const unsigned int rho = rest == 0 ? (unsigned int)(64 - HLL_P + 1) : (unsigned int)__clzll(rest) + 1u;
+        atomicMax(r + (h >> (64 - HLL_P)), rho);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < HLL_M; j += blockDim.x)
+        if (r[j]) atomicMax(regs + j, r[j]);
+}
+
+// Distinct-count estimate from the registers (harmonic mean, linear counting when small).
+double hll_estimate(const unsigned int* regs) {
+    double z = 0.0;
+    int zeros = 0;
+    for (int j = 0; j < HLL_M; ++j) {
+        z += std::ldexp(1.0, -(int)regs[j]);
+        zeros += regs[j] == 0;
+    }
+    const double m = HLL_M;
+    const double est = 0.7213 / (1.0 + 1.079 / m) * m * m / z;
+    if (est <= 2.5 * m && zeros > 0) return m * std::log(m / zeros);
+    return est;
+}
+
+// Set of distinct ids: linear probing over S slots.  A slot goes from empty to an id once,
+// so a stale empty read only leads to a compare-and-swap that returns the slot's real
+// content.  A probe sequence longer than `limit` sets *overflow and drops the id (the caller
+// then retries with a table of more slots than ids, where every sequence ends).
+__global__ void k_set_insert(const uint64_t* src, const uint64_t* dst, int64_t E, uint64_t* tab, uint64_t S,
+                             uint64_t limit, int* has_empty, int* overflow) {
+    constexpr int Q = 4;  // ids per thread and pass: their first probes are in flight together
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < 2 * E; i0 += Q * T) {
+        uint64_t x[Q], slot[Q], cur[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t i = i0 + q * T;
+            x[q] = i < 2 * E ? (i < E ? src[i] : dst[i - E]) : EMPTY_ID;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            slot[q] = __umul64hi(mix64(x[q] ^ 0x2545F4914F6CDD1Dull), S);
+            cur[q] = x[q] != EMPTY_ID ? tab[slot[q]] : EMPTY_ID;
+        }
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            if (x[q] == EMPTY_ID) {
+                if (i0 + q * T < 2 * E) atomicOr(has_empty, 1);
+                continue;
             }
+            uint64_t s = slot[q], c = cur[q];
+            uint64_t probe = 0;
+            for (; probe < limit; ++probe) {
+                if (c == x[q]) break;
+                if (c == EMPTY_ID) {
+                    const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(tab + s),
+                                                              (unsigned long long)EMPTY_ID,
+                                                              (unsigned long long)x[q]);
+                    if (prev == EMPTY_ID || prev == x[q]) break;
+                }
+                s = (s + 1 == S) ? 0 : s + 1;
+                c = tab[s];
+            }
+            if (probe == limit) atomicOr(overflow, 1);
+        }
+    }
+}
+
+struct NotEmptyId {
+    __device__ __forceinline__ bool operator()(uint64_t x) const { return x != EMPTY_ID; }
+};
+
+// id -> rank table: 2^k slots of {id, rank} (at least twice the ids), linear probing.
+__global__ void k_rank_insert(const uint64_t* ids, int64_t n, ulonglong2* tab, uint64_t mask) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = ids[i];
+        if (x == EMPTY_ID) continue;
+        uint64_t slot = mix64(x ^ 0x9E6C63D0676A9A99ull) & mask;
+        for (uint64_t probe = 0; probe <= mask; ++probe) {
+            const unsigned long long prev = atomicCAS(&tab[slot].x, (unsigned long long)EMPTY_ID,
+                                                      (unsigned long long)x);
+            if (prev == EMPTY_ID) {
+                tab[slot].y = (unsigned long long)i;
+                break;
+            }
+            slot = (slot + 1) & mask;
+        }
+    }
+}
+
+// First probe of id x in the id -> rank table (its home slot).
+__device__ __forceinline__ ulonglong2 tab_first(const ulonglong2* tab, uint64_t mask, uint64_t x) {
+    return tab[mix64(x ^ 0x9E6C63D0676A9A99ull) & mask];
+}
+
+// Rank of id x given its home slot's content `v`, or -1 when x is not in the table.
+__device__ __forceinline__ int64_t rank_resolve(const ulonglong2* tab, uint64_t mask, uint64_t x, ulonglong2 v,
+                                                int64_t n, bool has_empty) {
+    if (x == EMPTY_ID) return has_empty ? n - 1 : -1;
+    uint64_t slot = mix64(x ^ 0x9E6C63D0676A9A99ull) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        if (v.x == x) return (int64_t)v.y;
+        if (v.x == EMPTY_ID) return -1;
+        slot = (slot + 1) & mask;
+        v = tab[slot];
+    }
+    return -1;
+}
+
+// Entry key(s) of edge e from its endpoints' ranks.
+__device__ __forceinline__ void emit_entry(int64_t e, int64_t ra, int64_t rb, const float* w, int directed,
+                                           int bits, uint64_t invalid, uint64_t* keys, float* vals, int* missing) {
+    if (ra < 0 || rb < 0) {  // cannot happen: every endpoint went into the table
+        atomicOr(missing, 1);
+        keys[directed ? e : 2 * e] = invalid;
+        if (!directed) keys[2 * e + 1] = invalid;
+        return;
+    }
+    const uint64_t a = (uint64_t)ra, b = (uint64_t)rb;
+    if (directed) {
+        keys[e] = (a << bits) | b;
+        if (vals) vals[e] = w[e];
+    } else {
+        keys[2 * e] = (a << bits) | b;
+        keys[2 * e + 1] = (a == b) ? invalid : ((b << bits) | a);
+        if (vals) {
+            vals[2 * e] = w[e];
+            vals[2 * e + 1] = w[e];
+        }
+    }
+}
+
+__global__ void k_entries(const uint64_t* src, const uint64_t* dst, const float* w, int64_t E,
+                          int directed, const ulonglong2* rank_tab, uint64_t mask, int64_t n, int has_empty,
+                          int bits, uint64_t invalid, uint64_t* keys, float* vals, int* missing) {
+    constexpr int Q = 4;  // edges per thread and pass: 2Q first probes in flight together
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < E; e0 += Q * T) {
+        uint64_t x[2 * Q];
+        ulonglong2 v[2 * Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t e = e0 + q * T;
+            x[2 * q] = e < E ? src[e] : EMPTY_ID;
+            x[2 * q + 1] = e < E ? dst[e] : EMPTY_ID;
+        }
+#pragma unroll
+        for (int i = 0; i < 2 * Q; ++i)
+            v[i] = x[i] != EMPTY_ID ? tab_first(rank_tab, mask, x[i]) : make_ulonglong2(EMPTY_ID, 0);
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            const int64_t e = e0 + q * T;
+            if (e >= E) break;
+            const int64_t ra = rank_resolve(rank_tab, mask, x[2 * q], v[2 * q], n, has_empty != 0);
+            const int64_t rb = rank_resolve(rank_tab, mask, x[2 * q + 1], v[2 * q + 1], n, has_empty != 0);
+            emit_entry(e, ra, rb, w, directed, bits, invalid, keys, vals, missing);
         }
     }
 }
@@ -104,15 +266,13 @@ __global__ void k_runs(const uint64_t* keys, const float* vals, const int64_t* s
         const uint64_t key = keys[s];
         col[k] = (int32_t)(key & mask);
         row[k] = (int32_t)(key >> bits);
-        double acc;
         if (vals) {
-            acc = 0.0;
+            double acc = 0.0;
             for (int64_t i = s; i < t; ++i) acc = __dadd_rn(acc, (double)vals[i]);
-        } else {
-            acc = (double)(t - s);
-            if (t - s != 1) atomicOr(not_unit, 1);
+            e[k] = acc;
+        } else if (t - s != 1) {  // unweighted: e_ab = t - s, recomputed from the run starts
+            atomicOr(not_unit, 1);
         }
-        e[k] = acc;
     }
 }
 
@@ -125,31 +285,41 @@ __global__ void k_rowptr(const int32_t* row, int64_t nnz, int64_t n, int64_t* ro
     }
 }
 
-// Unweighted graphs: every e_ab is an integer count, so the row sum is exact in any order;
-// one warp per row (integer accumulation) keeps hub rows from becoming stragglers.
-__global__ void k_degree_int(const int64_t* rowptr, const double* e, int64_t n, double* deg,
-                             float* inv_deg, unsigned long long* max_len) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; r < n; r += warps) {
-        const int64_t b = rowptr[r], t = rowptr[r + 1];
-        long long acc = 0;
-        for (int64_t k = b + lane; k < t; k += 32) acc += (long long)e[k];
+// Largest row length: a warp maximum, then one atomic per warp (one atomic per row on the same
+// address serialises in L2).  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_max_out(unsigned long long* out, unsigned long long v) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) {
-            const double s = (double)acc;
-            deg[r] = s;
-            inv_deg[r] = s > 0.0 ? __fdiv_rn(1.0f, __double2float_rn(s)) : 0.0f;
-            atomicMax(max_len, (unsigned long long)(t - b));
-        }
+    for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
+}
+
+// Start of run k among the sorted raw entries (run nnz ends at the last valid entry).
+__device__ __forceinline__ int64_t run_start(const int64_t* start, int64_t nnz, const int64_t* m_valid, int64_t k) {
+    return k < nnz ? start[k] : *m_valid;
+}
+
+// Unweighted graphs: e_ab is the length of run k, so deg_a, the sum of the row's e_ab, is
+// the number of raw entries from the row's first run start to its last run end (an integer,
+// exact in any order).
+__global__ void k_degree_int(const int64_t* rowptr, const int64_t* start, int64_t nnz, const int64_t* m_valid,
+                             int64_t n, double* deg, float* inv_deg, unsigned long long* max_len) {
+    unsigned long long mx = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rowptr[r], t = rowptr[r + 1];
+        const double s = (double)(run_start(start, nnz, m_valid, t) - run_start(start, nnz, m_valid, b));
+        deg[r] = s;
+        inv_deg[r] = s > 0.0 ? __fdiv_rn(1.0f, __double2float_rn(s)) : 0.0f;
+        mx = max(mx, (unsigned long long)(t - b));
     }
+    warp_max_out(max_len, mx);
 }
 
 // Weighted graphs: deg_a is the FP64 sum of e_ab in ascending column order, one thread per
 // row (the order is part of the bit-exact definition of the stored values).
 __global__ void k_degree(const int64_t* rowptr, const double* e, int64_t n, double* deg,
                          float* inv_deg, unsigned long long* max_len) {
+    unsigned long long mx = 0;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = rowptr[r], t = rowptr[r + 1];
@@ -157,15 +327,19 @@ __global__ void k_degree(const int64_t* rowptr, const double* e, int64_t n, doub
         for (int64_t k = b; k < t; ++k) s = __dadd_rn(s, e[k]);
         deg[r] = s;
         inv_deg[r] = s > 0.0 ? __fdiv_rn(1.0f, __double2float_rn(s)) : 0.0f;
-        atomicMax(max_len, (unsigned long long)(t - b));
+        mx = max(mx, (unsigned long long)(t - b));
     }
+    warp_max_out(max_len, mx);
 }
 
-__global__ void k_values(const int32_t* row, const double* e, const double* deg, int64_t nnz,
-                         float* val) {
+// val = fp32(e_ab / deg_a); e_ab from the weights' sums, or (unweighted) the run length.
+__global__ void k_values(const int32_t* row, const double* e, const int64_t* start, const int64_t* m_valid,
+                         const double* deg, int64_t nnz, float* val) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
-         k += (int64_t)gridDim.x * blockDim.x)
-        val[k] = __double2float_rn(__ddiv_rn(e[k], deg[row[k]]));
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double ek = e ? e[k] : (double)(run_start(start, nnz, m_valid, k + 1) - start[k]);
+        val[k] = __double2float_rn(__ddiv_rn(ek, deg[row[k]]));
+    }
 }
 
 __global__ void k_broadcast_inv(const int64_t* rowptr, const float* inv_deg, int64_t n, float* val) {
@@ -191,6 +365,10 @@ struct DBuf {
     explicit DBuf(cleora_ctx* c) : ctx(c) {}
     ~DBuf() { dfree(ctx, p); }
     int alloc(size_t count) { return dalloc(ctx, &p, count ? count : 1); }
+    void reset() {
+        dfree(ctx, p);
+        p = nullptr;
+    }
     T* release() {
         T* q = p;
         p = nullptr;
@@ -233,36 +411,99 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     }
 
     const int64_t m = directed ? E : 2 * E;  // entries before dedup
-    DBuf<uint64_t> ka(ctx), kb(ctx);
-    CL_TRY(ka.alloc((size_t)(2 * E)));
-    CL_TRY(kb.alloc((size_t)(2 * E)));
+    // One buffer of 4E words: first the id set (load <= 1/2), then the two key buffers of
+    // the entry sort (2E words each).
+    DBuf<uint64_t> kk(ctx);
+    CL_TRY(kk.alloc((size_t)(4 * E)));
+    uint64_t* ka = kk.p;
+    uint64_t* kb = kk.p + 2 * E;
 
-    // 1. ids = sort-unique(src ++ dst)
-    CL_CUDA(ctx, cudaMemcpyAsync(ka.p, src, E * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-    CL_CUDA(ctx, cudaMemcpyAsync(ka.p + E, dst, E * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    // 1. ids = sorted distinct endpoints
+    int has_empty = 0;
+    DBuf<ulonglong2> rank_tab(ctx);
+    uint64_t rank_mask = 0;
     {
-        cub::DoubleBuffer<uint64_t> db(ka.p, kb.p);
+        // table size: 4x the sketch's distinct estimate (load about 1/4), at most 4E slots;
+        // probe sequences are capped unless the table has more slots than there are ids
+        const uint64_t S_full = (uint64_t)(4 * E);
+        uint64_t S = S_full;
+        if (E > 0) {
+            DBuf<unsigned int> regs(ctx);
+            CL_TRY(regs.alloc(HLL_M));
+            CL_CUDA(ctx, cudaMemsetAsync(regs.p, 0, HLL_M * sizeof(unsigned int), s));
+            k_hll<<<grid_for(2 * E, 256, sms), 256, 0, s>>>(src, dst, E, regs.p);
+            CL_LAUNCHED(ctx);
+            std::vector<unsigned int> hr(HLL_M);
+            CL_CUDA(ctx, cudaMemcpyAsync(hr.data(), regs.p, HLL_M * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+            CL_CUDA(ctx, cudaStreamSynchronize(s));
+            const double est = hll_estimate(hr.data());
+            uint64_t want = 1 << 16;
+            while ((double)want < 4.0 * est) want <<= 1;
+            S = std::min(S_full, want);
+        }
+        int* d_overflow = reinterpret_cast<int*>(scal.p + 2);
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            CL_CUDA(ctx, cudaMemsetAsync(kk.p, 0xff, S * sizeof(uint64_t), s));
+            if (E == 0) break;
+            k_set_insert<<<grid_for(2 * E, 256, sms), 256, 0, s>>>(src, dst, E, kk.p, S, S == S_full ? S : 4096,
+                                                                    d_flag, d_overflow);
+            CL_LAUNCHED(ctx);
+            int ovf = 0;
+            CL_CUDA(ctx, cudaMemcpyAsync(&ovf, d_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CL_CUDA(ctx, cudaStreamSynchronize(s));
+            if (!ovf) break;
+            if (S == S_full) return fail(ctx, CLEORA_ERR_DEVICE, "id set overflow");
+            S = S_full;  // the estimate was far off: retry with room for every endpoint
+            CL_CUDA(ctx, cudaMemsetAsync(d_overflow, 0, sizeof(int), s));
+        }
+        // count the distinct ids, then move them out of the table
+        DBuf<uint64_t> ua(ctx);
         size_t tb = 0;
-        CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(nullptr, tb, db, 2 * E, 0, 64, s));
+        NotEmptyId pred;
+        CL_CUDA(ctx, cub::DeviceSelect::If(nullptr, tb, kk.p, scal.p, (int64_t)S, pred, s));
         DBuf<unsigned char> tmp(ctx);
         CL_TRY(tmp.alloc(tb));
-        CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(tmp.p, tb, db, 2 * E, 0, 64, s));
-        uint64_t* sorted = db.Current();
-        uint64_t* other = db.Alternate();
-        size_t tu = 0;
-        CL_CUDA(ctx, cub::DeviceSelect::Unique(nullptr, tu, sorted, other, scal.p, 2 * E, s));
-        DBuf<unsigned char> tmp2(ctx);
-        CL_TRY(tmp2.alloc(tu));
-        CL_CUDA(ctx, cub::DeviceSelect::Unique(tmp2.p, tu, sorted, other, scal.p, 2 * E, s));
-        int64_t n = 0;
-        CL_CUDA(ctx, cudaMemcpyAsync(&n, scal.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        // in-place compaction keeps the selected ids in order at the front of the table
+        CL_CUDA(ctx, cub::DeviceSelect::If(tmp.p, tb, kk.p, scal.p, (int64_t)S, pred, s));
+        int64_t hv[2] = {0, 0};
+        CL_CUDA(ctx, cudaMemcpyAsync(hv, scal.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
+        has_empty = (int)(hv[1] & 0xffffffff);
+        const int64_t n = hv[0] + (has_empty ? 1 : 0);
         if (n >= ((int64_t)1 << 31))
             return fail(ctx, CLEORA_ERR_INVALID_ARG, "graph has %lld nodes; the limit is 2^31-1",
                         (long long)n);
+        CL_CUDA(ctx, cudaMemsetAsync(d_flag, 0, sizeof(int), s));
         g.n = n;
-        CL_TRY(dalloc(ctx, &g.ids, (size_t)n));
-        CL_CUDA(ctx, cudaMemcpyAsync(g.ids, other, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        CL_TRY(dalloc(ctx, &g.ids, (size_t)(n ? n : 1)));
+        if (hv[0] > 0) {
+            CL_TRY(ua.alloc((size_t)hv[0]));
+            CL_CUDA(ctx, cudaMemcpyAsync(ua.p, kk.p, hv[0] * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+            cub::DoubleBuffer<uint64_t> db(ua.p, g.ids);
+            size_t tsort = 0;
+            CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(nullptr, tsort, db, hv[0], 0, 64, s));
+            DBuf<unsigned char> tmps(ctx);
+            CL_TRY(tmps.alloc(tsort));
+            CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(tmps.p, tsort, db, hv[0], 0, 64, s));
+            if (db.Current() != g.ids)
+                CL_CUDA(ctx, cudaMemcpyAsync(g.ids, db.Current(), hv[0] * sizeof(uint64_t),
+                                             cudaMemcpyDeviceToDevice, s));
+        }
+        if (has_empty) {
+            const uint64_t e = EMPTY_ID;
+            CL_CUDA(ctx, cudaMemcpyAsync(g.ids + hv[0], &e, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+        }
+        // id -> rank table, at least twice as many slots as ids
+        uint64_t slots = 2;
+        while (slots < 2 * (uint64_t)n) slots <<= 1;
+        rank_mask = slots - 1;
+        CL_TRY(rank_tab.alloc((size_t)slots));
+        CL_CUDA(ctx, cudaMemsetAsync(rank_tab.p, 0xff, slots * sizeof(ulonglong2), s));
+        if (n > 0) {
+            k_rank_insert<<<grid_for(n, 256, sms), 256, 0, s>>>(g.ids, n, rank_tab.p, rank_mask);
+            CL_LAUNCHED(ctx);
+        }
+        CL_CUDA(ctx, cudaStreamSynchronize(s));  // the host-side copy of the sentinel id is done
     }
     const int64_t n = g.n;
 
@@ -274,17 +515,19 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         CL_TRY(va.alloc((size_t)m));
         CL_TRY(vb.alloc((size_t)m));
     }
-    const int64_t ns = (n + SAMPLE - 1) / SAMPLE;
-    DBuf<uint64_t> sample(ctx);
-    CL_TRY(sample.alloc((size_t)ns));
-    k_sample_ids<<<grid_for(ns, 256, sms), 256, 0, s>>>(g.ids, n, sample.p, ns);
-    CL_LAUNCHED(ctx);
-    k_entries<<<grid_for(E, 256, sms), 256, 0, s>>>(src, dst, w, E, directed, g.ids, n, sample.p, ns,
-                                                   bits, invalid, ka.p, w ? va.p : nullptr);
-    CL_LAUNCHED(ctx);
+    if (E > 0) {
+        k_entries<<<grid_for(E, 256, sms), 256, 0, s>>>(src, dst, w, E, directed, rank_tab.p, rank_mask, n,
+                                                       has_empty, bits, invalid, ka, w ? va.p : nullptr, d_flag);
+        CL_LAUNCHED(ctx);
+        int missing = 0;
+        CL_CUDA(ctx, cudaMemcpyAsync(&missing, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, cudaStreamSynchronize(s));
+        if (missing) return fail(ctx, CLEORA_ERR_DEVICE, "endpoint missing from the id table");
+    }
+    rank_tab.reset();
 
     g.directed = directed != 0;
-    return csr_from_entries(ctx, ka.p, kb.p, w ? va.p : nullptr, w ? vb.p : nullptr, m, 2 * E, n, bits,
+    return csr_from_entries(ctx, ka, kb, w ? va.p : nullptr, w ? vb.p : nullptr, m, 2 * E, n, bits,
                             invalid, g);
 }
 
@@ -347,9 +590,9 @@ int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float*
     g.nnz = nnz;
 
     DBuf<int32_t> rows(ctx);
-    DBuf<double> e(ctx);
+    DBuf<double> e(ctx);  // e_ab of weighted graphs (unweighted: run lengths, from `start`)
     CL_TRY(rows.alloc((size_t)nnz));
-    CL_TRY(e.alloc((size_t)nnz));
+    if (weighted) CL_TRY(e.alloc((size_t)nnz));
     CL_TRY(dalloc(ctx, &g.col, (size_t)(nnz ? nnz : 1)));
     k_runs<<<grid_for(nnz, 256, sms), 256, 0, s>>>(keys, vals, start, nnz, scal.p + 3, bits, g.col,
                                                    rows.p, e.p, d_flag);
@@ -365,8 +608,8 @@ int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float*
         k_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg,
                                                        reinterpret_cast<unsigned long long*>(scal.p + 2));
     else
-        k_degree_int<<<grid_for(n * 32, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg,
-                                                                reinterpret_cast<unsigned long long*>(scal.p + 2));
+        k_degree_int<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, start, nnz, scal.p + 3, n, g.deg, g.inv_deg,
+                                                           reinterpret_cast<unsigned long long*>(scal.p + 2));
     CL_LAUNCHED(ctx);
 
     int64_t hv[3] = {0, 0, 0};
@@ -379,7 +622,8 @@ int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float*
     // stored values
     if (g.has_val) {
         CL_TRY(dalloc(ctx, &g.val, (size_t)(nnz ? nnz : 1)));
-        k_values<<<grid_for(nnz, 256, sms), 256, 0, s>>>(rows.p, e.p, g.deg, nnz, g.val);
+        k_values<<<grid_for(nnz, 256, sms), 256, 0, s>>>(rows.p, weighted ? e.p : nullptr, start, scal.p + 3,
+                                                         g.deg, nnz, g.val);
         CL_LAUNCHED(ctx);
     }
     CL_CUDA(ctx, cudaStreamSynchronize(s));

@@ -171,9 +171,10 @@ int64_t cleora_serve_estimate(const cleora_job* j) {
     const int64_t es = j->storage == CLEORA_F32 ? 4 : 2;
     const int64_t w = j->weights ? 1 : 0;
     const int64_t MiB = (int64_t)1 << 20;
-    // graph build: uploads, two 2E-key sort buffers, run starts, sorted weights, CSR arrays
+    // graph build: uploads, the id set / two 2E-key sort buffers, the id -> rank table, run
+    // starts, sorted weights, CSR arrays
     const int64_t build = E * (16 + 4 * w) + 2 * (2 * E * 8) + (j->directed ? 0 : 8 * m) +
-                          w * 2 * 4 * m + m * (4 + 8 + 4) + n * 32 + 8 * m + 64 * MiB;
+                          w * 2 * 4 * m + m * (4 + 8 + 4) + n * 96 + 8 * m + 64 * MiB;
     // resident: CSR (+values), ids, rowptr, degrees; then plan build, then embeddings
     const int64_t resident = m * 8 + n * (8 + 8 + 4 + 8);
     const int64_t plan = resident + n * 53 + (m / 64 + 1) * 16;

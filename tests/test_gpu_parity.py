@@ -58,8 +58,31 @@ def assert_close_bf16(got, want):
     assert cos[nz].min() >= BF16_COS, f"min cosine {cos[nz].min():.6f}"
 
 
+def _extreme_ids():
+    """Ids at the ends of the uint64 range (0, 2^63, 2^64 - 2, 2^64 - 1) beside small dense
+    ids, with duplicates and a self-loop: the id hashing and the all-ones id."""
+    top = np.uint64(0xFFFFFFFFFFFFFFFF)
+    ids = np.array([0, 1, 2, 3, 1 << 63, (1 << 64) - 2, (1 << 64) - 1, 7, 8, 9], dtype=np.uint64)
+    assert ids[6] == top
+    u = np.array([0, 1, 2, 6, 6, 5, 4, 3, 9, 6, 6, 0, 8], dtype=np.int64)
+    v = np.array([1, 2, 6, 0, 5, 4, 3, 9, 6, 6, 8, 1, 7], dtype=np.int64)
+    return synth.EdgeList(ids[u], ids[v], None, False, len(ids))
+
+
+def _dense_ids():
+    """Directed weighted graph on the ids 0 .. n-1 (sequential ids, many sinks)."""
+    e = synth.random_multigraph(4000, 20000, 6, True, True)
+    ids = synth.node_ids(4000, 6)
+    rank = {int(x): i for i, x in enumerate(ids)}
+    src = np.array([rank[int(x)] for x in e.src], dtype=np.uint64)
+    dst = np.array([rank[int(x)] for x in e.dst], dtype=np.uint64)
+    return synth.EdgeList(src, dst, e.weights, True, 4000)
+
+
 GRAPHS = {
     "undirected_unit": lambda: synth.random_multigraph(300, 1500, 1, False, False, self_loops=False),
+    "extreme_ids": _extreme_ids,
+    "dense_ids": _dense_ids,
     "undirected_dups_loops": lambda: synth.random_multigraph(200, 2000, 2, False, False),
     "directed_weighted_sinks": lambda: synth.random_multigraph(500, 900, 3, True, True),
     "directed_unit_dups": lambda: synth.random_multigraph(257, 3000, 4, True, False),
@@ -286,3 +309,38 @@ def test_device_resident_inputs_and_outputs(graphs, oracle_graphs):
         ctx.sync()
         got = out.cpu().numpy()
     assert_close_f32(got, oracle.propagate(g, oracle.init(g.ids, 128, 5), 4))
+
+
+def test_pinned_host_buffers_match_pageable(graphs):
+    """Pinned host memory takes the direct path (conversion kernels read or write it over
+    the host link), pageable memory the staged one: both give the same bits, also at an
+    offset that is not 16-byte aligned."""
+    import torch
+    import paper_2102_02302_gb300 as pkg
+    e = graphs["power_law_small"]
+    d = 128
+    with _ctx() as ctx:
+        ctx.graph_build(e.src, e.dst, e.weights, e.directed)
+        n = ctx.info()["n"]
+        ctx.init(d, 0, "bf16")
+        ctx.propagate(2)
+        page = np.empty((n, d), np.float32)
+        pinned = torch.empty((n, d), dtype=torch.float32, pin_memory=True)
+        pkg.cleora_get_embeddings(ctx.handle, page, "f32")
+        pkg.cleora_get_embeddings(ctx.handle, pinned, "f32")
+        assert np.array_equal(page.view(np.uint32), pinned.numpy().view(np.uint32))
+        flat = torch.empty(n * d + 1, dtype=torch.float32, pin_memory=True)  # 4-byte offset
+        pkg.cleora_get_embeddings(ctx.handle, flat[1:], "f32")
+        assert np.array_equal(page.reshape(-1).view(np.uint32), flat[1:].numpy().view(np.uint32))
+        # FP32 rows in, BF16 storage: rounding on import is the same on both paths
+        rng = np.random.default_rng(3)
+        x = rng.standard_normal((n, d)).astype(np.float32)
+        xp = torch.from_numpy(x).pin_memory()
+        ctx.set_embeddings(x, "f32")
+        a = torch.empty((n, d), dtype=torch.bfloat16)
+        pkg.cleora_get_embeddings(ctx.handle, a, "bf16")
+        ctx.set_embeddings(xp, "f32")
+        b = torch.empty((n, d), dtype=torch.bfloat16)
+        pkg.cleora_get_embeddings(ctx.handle, b, "bf16")
+        assert torch.equal(a.view(torch.int16), b.view(torch.int16))
+        assert np.array_equal(a.view(torch.int16).numpy().astype(np.uint16), bf16_bits(x))
