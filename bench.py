@@ -299,7 +299,25 @@ def time_dtype(pkg, ctx, edges, spec, storage, steps, warmup, events_ok=True):
             "wall_s": wall, "launches": launches}
 
 
-def e2e_measure(pkg, spec, host_edges, storage, steps, device):
+def e2e_buffers(spec, edges):
+    """Pinned host buffers of the end-to-end measurement: the edge list and room for the
+    FP32 result (at most spec.n rows).  Allocated once, early, like an application's
+    long-lived staging buffers."""
+    import torch
+
+    def pinned_copy(t):  # a pinned host buffer filled straight from the device tensor
+        if t is None:
+            return None
+        h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+        h.copy_(t)
+        return h
+
+    src_h, dst_h, w_h = (pinned_copy(t) for t in edges[:3])
+    out = torch.empty((spec.n, spec.d), dtype=torch.float32, pin_memory=True)
+    return (src_h, dst_h, w_h), out
+
+
+def e2e_measure(pkg, spec, host_edges, out_buf, storage, steps, device):
     """Through the public API with host buffers: upload + build + init + I iterations +
     FP32 result back to host, every step."""
     import torch
@@ -307,7 +325,7 @@ def e2e_measure(pkg, spec, host_edges, storage, steps, device):
     with pkg.Context(device) as ctx:
         ctx.graph_build(src_h, dst_h, w_h, spec.directed)
         n = ctx.info()["n"]
-        out = torch.empty((n, spec.d), dtype=torch.float32, pin_memory=True)
+        out = out_buf[:n]
         times, phases = [], []
         for s in range(steps + 1):  # first one warms the pool
             t = time.perf_counter()
@@ -634,6 +652,8 @@ def main():
     t = time.perf_counter()
     edges = make_edges(spec, torch.device("cuda", device))
     gen_s = time.perf_counter() - t
+    if not args.no_e2e and rank == 0:
+        e2e_host, e2e_out = e2e_buffers(spec, edges)
 
     # A dedicated stream: the library and the CUDA events must share it (torch's default
     # stream has handle 0, which the C ABI reads as "create a private stream").
@@ -689,17 +709,9 @@ def main():
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        def pinned_copy(t):  # a pinned host buffer filled straight from the device tensor
-            if t is None:
-                return None
-            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
-            h.copy_(t)
-            return h
-
-        src_h, dst_h, w_h = (pinned_copy(t) for t in edges[:3])
         del edges
         torch.cuda.empty_cache()
-        t_e2e, h2d, d2h, split = e2e_measure(pkg, spec, (src_h, dst_h, w_h), head, args.e2e_steps, device)
+        t_e2e, h2d, d2h, split = e2e_measure(pkg, spec, e2e_host, e2e_out, head, args.e2e_steps, device)
         e2e = {"value": world * nnz * d * spec.iters / t_e2e, "unit": "nnz*d/s per iteration",
                "s_per_step": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "phases": split,

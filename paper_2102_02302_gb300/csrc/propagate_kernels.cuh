@@ -20,16 +20,21 @@
 //    neighbour rows and normalises.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 // Compile-time tuning knobs, chosen per storage type from measurements on GB300 (the
 // 1.4B-edge power-law graph, d = 128):
-//   FP32: one batch path, scalar FP32 adds, >= 4 CTAs/SM;
-//   BF16: a separate full-batch path, paired FP32 adds (-3.5% time), >= 4 CTAs/SM;
-//   both: 8 gathered vectors in flight per lane, and L2 policies on the gathers of
-//   partitioned rows (hot segment evict_last, cold segment evict_first).  Rows are
-//   partitioned only for graphs whose T is much larger than the hot-row budget; the policy of
-//   a segment is uniform, so it costs no per-entry work.
+//   FP32: one batch path, scalar FP32 adds, >= 4 CTAs/SM, 8 gathered vectors in flight per
+//         lane (it moves DRAM bytes at the copy bandwidth; occupancy changes nothing);
+//   BF16: a separate full-batch path, paired FP32 adds (-3.5% time), 4 vectors in flight per
+//         lane and as many CTAs/SM as the shape fits without spilling (8 for d = 128: -10%
+//         time against 4 CTAs with 8 in flight; latency-bound, so more warps beat deeper
+//         batches);
+//   both: L2 policies on the gathers of partitioned rows (hot segment evict_last, cold
+//   segment evict_first).  Rows are partitioned only for graphs whose T is much larger than
+//   the hot-row budget; the policy of a segment is uniform, so it costs no per-entry work.
 // A -D on the command line overrides the choice for both types (experiments).
 #ifndef CLEORA_COLD_POLICY
 #define CLEORA_COLD_POLICY 0   // gathers of unmarked rows: 0 evict_first, 1 evict_normal
@@ -98,8 +103,8 @@ template <> struct Tune<float> {
 #else
     static constexpr bool FULLB = false;
 #endif
-#ifdef CLEORA_MIN_BLOCKS
-    static constexpr int MINB = CLEORA_MIN_BLOCKS;
+#ifdef CLEORA_MIN_BLOCKS_F32
+    static constexpr int MINB = CLEORA_MIN_BLOCKS_F32;
 #else
     static constexpr int MINB = 4;
 #endif
@@ -125,15 +130,15 @@ template <> struct Tune<__nv_bfloat16> {
 #else
     static constexpr bool FULLB = true;
 #endif
-#ifdef CLEORA_MIN_BLOCKS
-    static constexpr int MINB = CLEORA_MIN_BLOCKS;
+#ifdef CLEORA_MIN_BLOCKS_BF16
+    static constexpr int MINB = CLEORA_MIN_BLOCKS_BF16;
 #else
-    static constexpr int MINB = 4;
+    static constexpr int MINB = 0;  // per shape: min_blocks() below
 #endif
 #ifdef CLEORA_INFLIGHT_BF16
     static constexpr int INFLIGHT = CLEORA_INFLIGHT_BF16;
 #else
-    static constexpr int INFLIGHT = 8;
+    static constexpr int INFLIGHT = 4;
 #endif
 #ifdef CLEORA_PACKED_BF16
     static constexpr bool PACKED = CLEORA_PACKED_BF16;
@@ -596,8 +601,22 @@ struct Kern {
     }
 };
 
+// CTAs per SM the kernel is compiled for (its register budget is 65536 / (256 x that)).
+// Rows of more than two vectors per lane leave it to the compiler.  BF16: as many as the shape
+// fits without spilling (measured by ptxas at 4 vectors in flight); FP32: Tune's count.
+template <typename ST, int VEC, int CPL, int G, bool HV>
+constexpr int min_blocks() {
+    if (CPL > 2) return 1;
+    if (!std::is_same<ST, __nv_bfloat16>::value) return Tune<ST>::MINB;
+    if (Tune<ST>::MINB > 0) return Tune<ST>::MINB;
+    if (G < 32) return 4;
+    if (VEC == 8 && CPL == 1) return HV ? 6 : 8;
+    if (VEC == 16 && CPL == 2) return 4;
+    return 6;
+}
+
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
-__global__ void __launch_bounds__(256, (Tune<ST>::MINB > 0 && CPL <= 2) ? Tune<ST>::MINB : 1)
+__global__ void __launch_bounds__(256, (min_blocks<ST, VEC, CPL, G, HV>()))
 k_propagate(Args a) {
     using K = Kern<ST, VEC, CPL, G, HV>;
     const int lane = threadIdx.x & 31;
