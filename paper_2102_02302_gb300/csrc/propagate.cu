@@ -119,28 +119,20 @@ __global__ void k_bins(const uint32_t* cnt, int64_t n, uint8_t* bin, unsigned lo
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
-// Hot flags of 32 consecutive entries as one bit word per thread, and the word's count.
+// Hot flags of 32 consecutive entries as one bit word (a warp per word, a lane per entry:
+// coalesced loads and one ballot), and the word's count.
 __global__ void k_hot_words(const int32_t* col, int64_t nnz, const uint8_t* bin, int threshold, uint32_t* word,
                             int64_t* cnt, int64_t nw) {
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k0 = w * 32;
-        uint32_t bits = 0;
-        if (k0 + 32 <= nnz) {
-            const int4* p = reinterpret_cast<const int4*>(col + k0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int4 c = __ldcs(p + q);
-                bits |= (uint32_t)(bin[c.x] >= threshold) << (4 * q);
-                bits |= (uint32_t)(bin[c.y] >= threshold) << (4 * q + 1);
-                bits |= (uint32_t)(bin[c.z] >= threshold) << (4 * q + 2);
-                bits |= (uint32_t)(bin[c.w] >= threshold) << (4 * q + 3);
-            }
-        } else {
-            for (int j = 0; k0 + j < nnz; ++j) bits |= (uint32_t)(bin[col[k0 + j]] >= threshold) << j;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
+        const int64_t k = w * 32 + lane;
+        const bool hot = k < nnz && bin[__ldcs(col + k)] >= threshold;
+        const uint32_t bits = __ballot_sync(0xffffffffu, hot);
+        if (lane == 0) {
+            word[w] = bits;
+            cnt[w] = __popc(bits);
         }
-        word[w] = bits;
-        cnt[w] = __popc(bits);
     }
 }
 
@@ -174,45 +166,44 @@ __device__ __forceinline__ int64_t row_of(const int64_t* rowptr, int64_t k, int6
     return lo;
 }
 
-// Stable hot-first partition of every row: thread per 32-entry word, 256 words per block.  A
-// hot entry k of row [beg, end) goes to beg + (hot entries of the row before k); a cold one
-// after the row's hot part, to k - H(k) + H(end), H(p) = hot entries in [0, p).
+// Stable hot-first partition of every row.  A warp takes a run of 32-entry words and one
+// word at a time, a lane per entry, so that loads are coalesced and a row's hot entries (and
+// its cold ones) are stored by consecutive lanes to consecutive places.  A hot entry k of row
+// [beg, end) goes to beg + (hot entries of the row before k); a cold one after the row's hot
+// part, to k - H(k) + H(end), H(p) = hot entries in [0, p).
+constexpr int SCATTER_WORDS = 32;  // words per warp task
+
 __global__ void __launch_bounds__(256) k_hot_scatter(const int64_t* rowptr, int64_t n, const int32_t* col,
                                                      const float* val, int64_t nnz, const uint32_t* word,
                                                      const int64_t* base, int64_t nw, const int64_t* rowH,
                                                      int32_t* col2, float* val2) {
-    __shared__ int64_t s_lo, s_hi;
-    for (int64_t wb = blockIdx.x * 256ll; wb < nw; wb += (int64_t)gridDim.x * 256ll) {
-        if (threadIdx.x == 0) {
-            s_lo = row_of(rowptr, wb * 32, 0, n - 1);
-            s_hi = row_of(rowptr, min(nnz, (wb + 256) * 32) - 1, s_lo, n - 1);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = warp * SCATTER_WORDS; w0 < nw; w0 += nwarps * SCATTER_WORDS) {
+        const int64_t w1 = min(nw, w0 + SCATTER_WORDS);
+        int64_t lo = 0, hi = 0;  // rows holding the task's first and last entries
+        if (lane == 0) {
+            lo = row_of(rowptr, w0 * 32, 0, n - 1);
+            hi = row_of(rowptr, min(nnz, w1 * 32) - 1, lo, n - 1);
         }
-        __syncthreads();
-        const int64_t w = wb + threadIdx.x;
-        if (w < nw) {
-            const int64_t k0 = w * 32;
-            const int m = (int)min((int64_t)32, nnz - k0);
-            int64_t r = row_of(rowptr, k0, s_lo, s_hi);
-            int64_t beg = rowptr[r], end = rowptr[r + 1], hb = rowH[r], he = rowH[r + 1];
-            int64_t H = base[w];
+        lo = __shfl_sync(FULL, lo, 0);
+        hi = __shfl_sync(FULL, hi, 0);
+        for (int64_t w = w0; w < w1; ++w) {
+            const int64_t k = w * 32 + lane;
             const uint32_t bits = word[w];
-            for (int j = 0; j < m; ++j) {
-                const int64_t k = k0 + j;
-                while (k >= end) {
-                    ++r;
-                    beg = end;
-                    end = rowptr[r + 1];
-                    hb = he;
-                    he = rowH[r + 1];
-                }
-                const bool hot = (bits >> j) & 1u;
-                const int64_t pos = hot ? beg + (H - hb) : k - H + he;
+            int64_t r = hi;
+            if (k < nnz) {
+                r = row_of(rowptr, k, lo, hi);
+                const bool hot = (bits >> lane) & 1u;
+                const int64_t H = base[w] + __popc(bits & ((1u << lane) - 1u));
+                const int64_t pos = hot ? rowptr[r] + (H - rowH[r]) : k - H + rowH[r + 1];
                 col2[pos] = col[k];
                 if (val) val2[pos] = val[k];
-                H += hot ? 1 : 0;
             }
+            lo = __shfl_sync(FULL, r, 31);  // the next word starts in this word's last row
         }
-        __syncthreads();
     }
 }
 
@@ -478,7 +469,7 @@ int hot_partition(cleora_ctx* ctx) {
         if ((rc = dalloc(ctx, &hot_cnt, (size_t)g.n))) break;
         if ((rc = dalloc(ctx, &col2, (size_t)g.nnz))) break;
         if (g.has_val && (rc = dalloc(ctx, &val2, (size_t)g.nnz))) break;
-        k_hot_words<<<grid_for(nw, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, threshold, word, wcnt, nw);
+        k_hot_words<<<grid_for(nw * 32, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, threshold, word, wcnt, nw);
         ctx->launches++;
         size_t tb = 0;
         e = cub::DeviceScan::ExclusiveSum(nullptr, tb, wcnt, wcnt, nw, s);
@@ -488,7 +479,7 @@ int hot_partition(cleora_ctx* ctx) {
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
         ctx->launches++;
         k_row_hot<<<grid_for(g.n, 256, sms), 256, 0, s>>>(g.rowptr, g.n, word, wcnt, nw, rowH, hot_cnt);
-        const int64_t blocks = std::min<int64_t>((nw + 255) / 256, (int64_t)sms * 8);
+        const int64_t blocks = std::min<int64_t>((nw + 8 * SCATTER_WORDS - 1) / (8 * SCATTER_WORDS), (int64_t)sms * 8);
         k_hot_scatter<<<(unsigned)blocks, 256, 0, s>>>(g.rowptr, g.n, g.col, g.has_val ? g.val : nullptr, g.nnz,
                                                        word, wcnt, nw, rowH, col2, val2);
         ctx->launches += 2;
