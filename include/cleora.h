@@ -137,13 +137,18 @@ typedef enum {
     CLEORA_OPT_SPLIT_LEN = 2,    /* rows longer than this are split across warps (>= 256)  */
     CLEORA_OPT_TASK_NNZ = 3,     /* entries per scheduled task (>= 64)                      */
     CLEORA_OPT_BLOCKS_PER_SM = 4, /* persistent CTAs per SM; 0 = occupancy limit           */
-    CLEORA_OPT_HOT_BYTES = 5     /* L2 bytes kept for the rows most entries point at:
+    CLEORA_OPT_HOT_BYTES = 5,    /* L2 bytes kept for the rows most entries point at:
                                     cleora_init moves the entries that point at them to the
                                     front of their rows (gathered with an evict_last
                                     policy, the rest evict_first) when T is larger than
                                     twice this; 0 = 72 MiB, 1 = off.  Only the summation
                                     order changes; cleora_get_csr still returns each row
                                     in ascending column order                              */
+    CLEORA_OPT_ID_SLOTS = 6      /* slots of the hash set that collects the distinct ids in
+                                    cleora_graph_build; 0 = four times a HyperLogLog
+                                    estimate of their number.  A set that fills up is
+                                    rebuilt with 4 x num_edges slots, so any value gives the
+                                    same graph                                             */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);

@@ -477,6 +477,9 @@ int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value) {
         case CLEORA_OPT_HOT_BYTES:
             if (value < 0) return fail(ctx, CLEORA_ERR_INVALID_ARG, "hot bytes");
             break;
+        case CLEORA_OPT_ID_SLOTS:
+            if (value < 0) return fail(ctx, CLEORA_ERR_INVALID_ARG, "id slots");
+            break;
         default:
             return fail(ctx, CLEORA_ERR_INVALID_ARG, "unknown option");
     }

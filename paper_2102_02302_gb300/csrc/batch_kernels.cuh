@@ -92,8 +92,16 @@ __device__ __forceinline__ void dispatch(int variant, const prop::Args& a, const
 }
 #undef CLEORA_BV
 
+// BF16 families are compiled for 4 CTAs/SM (64 registers): the dispatch over every variant
+// of a family otherwise takes 94-110 registers, 2 CTAs/SM.  Measured on the 4096-graph batch:
+// 153 ms per replay unbounded, 125 ms at 3 CTAs, 113 ms at 4 (despite some spilling in the
+// 16-byte family).
+#ifndef CLEORA_BATCH_MINB
+#define CLEORA_BATCH_MINB 4
+#endif
 template <typename ST, int VEC, int CPL>
-__global__ void __launch_bounds__(256) k_batch(BatchArgs ba) {
+__global__ void __launch_bounds__(256, (std::is_same<ST, __nv_bfloat16>::value && CPL <= 2) ? CLEORA_BATCH_MINB : 1)
+k_batch(BatchArgs ba) {
     const int lane = threadIdx.x & 31;
     const bool odd = ba.step & 1;
     for (;;) {

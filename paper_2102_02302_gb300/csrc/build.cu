@@ -427,7 +427,9 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         // probe sequences are capped unless the table has more slots than there are ids
         const uint64_t S_full = (uint64_t)(4 * E);
         uint64_t S = S_full;
-        if (E > 0) {
+        if (E > 0 && ctx->opt[CLEORA_OPT_ID_SLOTS] > 0) {
+            S = std::min<uint64_t>(S_full, (uint64_t)ctx->opt[CLEORA_OPT_ID_SLOTS]);
+        } else if (E > 0) {
             DBuf<unsigned int> regs(ctx);
             CL_TRY(regs.alloc(HLL_M));
             CL_CUDA(ctx, cudaMemsetAsync(regs.p, 0, HLL_M * sizeof(unsigned int), s));

@@ -61,7 +61,7 @@ struct Shape {
     int chunks = 0; // vectors per row
 };
 
-enum { OPT_COUNT = 6 };
+enum { OPT_COUNT = 7 };
 
 constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
 constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
@@ -87,7 +87,7 @@ struct cleora_ctx {
     int cur = 0;
     int iteration = 0;
 
-    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0};
+    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0};
     int* err_flag = nullptr;  // device int, raised by kernels
     int64_t launches = 0;
     int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails

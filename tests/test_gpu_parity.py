@@ -344,3 +344,19 @@ def test_pinned_host_buffers_match_pageable(graphs):
         pkg.cleora_get_embeddings(ctx.handle, b, "bf16")
         assert torch.equal(a.view(torch.int16), b.view(torch.int16))
         assert np.array_equal(a.view(torch.int16).numpy().astype(np.uint16), bf16_bits(x))
+
+
+@pytest.mark.parametrize("slots", [1, 64, 1 << 20, 0])
+def test_id_set_size_does_not_change_the_graph(slots, graphs, oracle_graphs):
+    """The distinct-id hash set: a set too small for the ids (1 or 64 slots) fills up and
+    is rebuilt with room for every endpoint; any size gives the same ids and CSR."""
+    for name in ("power_law_small", "extreme_ids"):
+        e, g = graphs[name], oracle_graphs[name]
+        with _ctx() as ctx:
+            ctx.set_option("id_slots", slots)
+            ctx.graph_build(e.src, e.dst, e.weights, e.directed)
+            c = ctx.csr()
+            ids = ctx.node_ids()
+        assert np.array_equal(ids, g.ids)
+        assert np.array_equal(c["rowptr"], g.rowptr) and np.array_equal(c["col"], g.col)
+        assert np.array_equal(c["deg"].view(np.uint64), g.deg.view(np.uint64))
