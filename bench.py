@@ -410,6 +410,7 @@ def batch_measure(device, steps, warmup, count=4096):
         for _ in range(warmup):
             b.run(None)
         times = []
+        torch.cuda.nvtx.range_push("timed_batch")  # lets a profiler keep only timed launches
         with torch.cuda.stream(stream):
             for _ in range(steps):
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -419,6 +420,7 @@ def batch_measure(device, steps, warmup, count=4096):
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
         run_ms = float(np.median(times))
         launches = b.launches()
     return {"graphs": count, "storage": "bf16", "nodes": tot["nodes"], "nnz": tot["nnz"],

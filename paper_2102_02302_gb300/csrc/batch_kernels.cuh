@@ -61,7 +61,8 @@ constexpr int variant_of(int G, int mode, bool hv) {
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
 __device__ __forceinline__ void run_task(const prop::Args& a, const Task& t, int lane) {
-    using K = prop::Kern<ST, VEC, CPL, G, HV>;
+    // 4 vectors in flight for BF16 families (measured with the 4-CTA bound below)
+    using K = prop::Kern<ST, VEC, CPL, G, HV, false, std::is_same<ST, __nv_bfloat16>::value ? 4 : 0>;
     const int g = lane / G, lg = lane % G;
     if (t.c >= 0) K::split_chunk(a, t, lane, g, lg);
     else if (MODE == 1 || G == 32) K::rows_coop(a, t.a, t.b, lane, g, lg);

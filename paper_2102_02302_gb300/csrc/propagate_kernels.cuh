@@ -28,10 +28,10 @@
 // 1.4B-edge power-law graph, d = 128):
 //   FP32: one batch path, scalar FP32 adds, >= 4 CTAs/SM, 8 gathered vectors in flight per
 //         lane (it moves DRAM bytes at the copy bandwidth; occupancy changes nothing);
-//   BF16: a separate full-batch path, paired FP32 adds (-3.5% time), 4 vectors in flight per
-//         lane and as many CTAs/SM as the shape fits without spilling (8 for d = 128: -10%
-//         time against 4 CTAs with 8 in flight; latency-bound, so more warps beat deeper
-//         batches);
+//   BF16: a separate full-batch path, paired FP32 adds (-3.5% time); 8-byte whole-warp rows
+//         (d = 128) at 8 CTAs/SM with 4 vectors in flight per lane (-10% time against 4 CTAs
+//         with 8: latency-bound, so more warps beat deeper batches), other shapes at 4 CTAs
+//         with 8 in flight;
 //   both: L2 policies on the gathers of partitioned rows (hot segment evict_last, cold
 //   segment evict_first).  Rows are partitioned only for graphs whose T is much larger than
 //   the hot-row budget; the policy of a segment is uniform, so it costs no per-entry work.
@@ -138,7 +138,7 @@ template <> struct Tune<__nv_bfloat16> {
 #ifdef CLEORA_INFLIGHT_BF16
     static constexpr int INFLIGHT = CLEORA_INFLIGHT_BF16;
 #else
-    static constexpr int INFLIGHT = 4;
+    static constexpr int INFLIGHT = 0;  // per shape: inflight() below
 #endif
 #ifdef CLEORA_PACKED_BF16
     static constexpr bool PACKED = CLEORA_PACKED_BF16;
@@ -239,13 +239,25 @@ template <> struct EL<__nv_bfloat16> {
 
 // CHECK: verify every column index against n (a CSR that does not come from this library's
 // own build); otherwise the index is trusted.
-template <typename ST, int VEC, int CPL, int G, bool HV, bool CHECK = false>
+// Gathered vectors in flight per lane and batch.  BF16 rows of 8-byte gathers over a whole
+// warp (d = 128) run at full occupancy with 4 (latency-bound: more warps beat deeper
+// batches); every other shape keeps 8 at 4 CTAs/SM (BF16 d = 256 on the 2M-node graph:
+// 3.3 ms against 5.1 ms with 4 in flight at 6 CTAs/SM).
+template <typename ST, int VEC, int CPL, int G>
+constexpr int inflight() {
+    if (Tune<ST>::INFLIGHT > 0) return Tune<ST>::INFLIGHT;
+    return (VEC == 8 && CPL == 1 && G == 32) ? 4 : 8;
+}
+
+// INF: vectors in flight per lane (0: inflight()).
+template <typename ST, int VEC, int CPL, int G, bool HV, bool CHECK = false, int INF = 0>
 struct Kern {
     using VT = typename VecT<VEC>::T;
     static constexpr int W = VEC / 4;                       // 32-bit words per vector
     static constexpr int EPV = W * EL<ST>::PER_WORD;        // elements per vector
     static constexpr int P = 32 / G;                        // lane groups per warp
-    static constexpr int U = CPL >= Tune<ST>::INFLIGHT ? 1 : Tune<ST>::INFLIGHT / CPL;  // entries per batch
+    static constexpr int IN = INF > 0 ? INF : inflight<ST, VEC, CPL, G>();
+    static constexpr int U = CPL >= IN ? 1 : IN / CPL;  // entries per batch
 
     // Two-level sum: `v` collects at most one 32-entry window, then is added into `t`.  Every
     // serial FP32 chain stays short (window + windows-per-row) even for a row of thousands of
@@ -602,17 +614,16 @@ struct Kern {
 };
 
 // CTAs per SM the kernel is compiled for (its register budget is 65536 / (256 x that)).
-// Rows of more than two vectors per lane leave it to the compiler.  BF16: as many as the shape
-// fits without spilling (measured by ptxas at 4 vectors in flight); FP32: Tune's count.
+// Rows of more than two vectors per lane leave it to the compiler.  BF16 8-byte whole-warp
+// rows: as many as fit without spilling at 4 vectors in flight (8, or 6 with per-entry
+// values); every other shape: Tune's count (FP32) or 4.
 template <typename ST, int VEC, int CPL, int G, bool HV>
 constexpr int min_blocks() {
     if (CPL > 2) return 1;
     if (!std::is_same<ST, __nv_bfloat16>::value) return Tune<ST>::MINB;
     if (Tune<ST>::MINB > 0) return Tune<ST>::MINB;
-    if (G < 32) return 4;
-    if (VEC == 8 && CPL == 1) return HV ? 6 : 8;
-    if (VEC == 16 && CPL == 2) return 4;
-    return 6;
+    if (VEC == 8 && CPL == 1 && G == 32) return HV ? 6 : 8;  // no spills at 4 in flight
+    return 4;
 }
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
