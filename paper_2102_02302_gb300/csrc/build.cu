@@ -184,18 +184,25 @@ __device__ __forceinline__ int64_t rank_resolve(const ulonglong2* tab, uint64_t 
     return -1;
 }
 
-// Entry key(s) of edge e from its endpoints' ranks.
-__device__ __forceinline__ void emit_entry(int64_t e, int64_t ra, int64_t rb, const float* w, int directed,
+// Entry key(s) of edge e from its endpoints' ranks.  `mode`: KEYS_DIRECTED one key (a, b);
+// KEYS_PAIR (undirected) keys (a, b) and (b, a) at 2e, 2e + 1 (a self-loop once);
+// KEYS_SYM (undirected) one key (min, max), the lower half being built later by transposing.
+enum { KEYS_PAIR = 0, KEYS_DIRECTED = 1, KEYS_SYM = 2 };
+
+__device__ __forceinline__ void emit_entry(int64_t e, int64_t ra, int64_t rb, const float* w, int mode,
                                            int bits, uint64_t invalid, uint64_t* keys, float* vals, int* missing) {
     if (ra < 0 || rb < 0) {  // cannot happen: every endpoint went into the table
         atomicOr(missing, 1);
-        keys[directed ? e : 2 * e] = invalid;
-        if (!directed) keys[2 * e + 1] = invalid;
+        keys[mode != KEYS_PAIR ? e : 2 * e] = invalid;
+        if (mode == KEYS_PAIR) keys[2 * e + 1] = invalid;
         return;
     }
     const uint64_t a = (uint64_t)ra, b = (uint64_t)rb;
-    if (directed) {
+    if (mode == KEYS_DIRECTED) {
         keys[e] = (a << bits) | b;
+        if (vals) vals[e] = w[e];
+    } else if (mode == KEYS_SYM) {
+        keys[e] = a <= b ? ((a << bits) | b) : ((b << bits) | a);
         if (vals) vals[e] = w[e];
     } else {
         keys[2 * e] = (a << bits) | b;
@@ -208,7 +215,7 @@ __device__ __forceinline__ void emit_entry(int64_t e, int64_t ra, int64_t rb, co
 }
 
 __global__ void k_entries(const uint64_t* src, const uint64_t* dst, const float* w, int64_t E,
-                          int directed, const ulonglong2* rank_tab, uint64_t mask, int64_t n, int has_empty,
+                          int mode, const ulonglong2* rank_tab, uint64_t mask, int64_t n, int has_empty,
                           int bits, uint64_t invalid, uint64_t* keys, float* vals, int* missing) {
     constexpr int Q = 4;  // edges per thread and pass: 2Q first probes in flight together
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
@@ -230,7 +237,7 @@ __global__ void k_entries(const uint64_t* src, const uint64_t* dst, const float*
             if (e >= E) break;
             const int64_t ra = rank_resolve(rank_tab, mask, x[2 * q], v[2 * q], n, has_empty != 0);
             const int64_t rb = rank_resolve(rank_tab, mask, x[2 * q + 1], v[2 * q + 1], n, has_empty != 0);
-            emit_entry(e, ra, rb, w, directed, bits, invalid, keys, vals, missing);
+            emit_entry(e, ra, rb, w, mode, bits, invalid, keys, vals, missing);
         }
     }
 }
@@ -376,6 +383,87 @@ struct DBuf {
     }
 };
 
+// --- undirected graphs from one (lo, hi) key per edge -----------------------------------
+// Row r of the symmetric CSR is [lo < r of the pairs (lo, r)] ++ [the pairs (r, hi), hi >= r]:
+// the second part is the sorted unique pairs' run of lo = r; the first part comes from the
+// same pairs sorted stably by hi (ascending lo within each hi, as the pairs are sorted by lo).
+
+// Multiplicities of unweighted pairs as FP64 (only when some pair repeats).
+__global__ void k_counts_to_e(const int64_t* start, int64_t nu, int64_t m_valid, double* e) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
+         u += (int64_t)gridDim.x * blockDim.x)
+        e[u] = (double)((u + 1 < nu ? start[u + 1] : m_valid) - start[u]);
+}
+
+// Keys of the transposed half: hi, or n for a self-loop (no transposed copy; sorts last).
+__global__ void k_transpose_keys(const int32_t* lo, const int32_t* hi, int64_t nu, uint32_t n, uint32_t* tk,
+                                 uint32_t* tv) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        tk[u] = lo[u] == hi[u] ? n : (uint32_t)hi[u];
+        tv[u] = (uint32_t)u;
+    }
+}
+
+// Number of sorted keys below n (the transposed entries; self-loop keys n come last).
+__global__ void k_count_below(const uint32_t* tk, int64_t nu, uint32_t n, int64_t* out) {
+    int64_t lo = 0, hi = nu;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tk[mid] < n) lo = mid + 1; else hi = mid;
+    }
+    *out = lo;
+}
+
+__global__ void k_add_rowptr(const int64_t* a, const int64_t* b, int64_t n, int64_t* out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[r] = a[r] + b[r];
+}
+
+// Lower part of each row: transposed entry i (row tk[i], pair tv[i]) at its rank in the row.
+__global__ void k_place_low(const uint32_t* tk, const uint32_t* tv, int64_t nt, const int64_t* rowptr,
+                            const int64_t* lowptr, const int32_t* lo, const double* e_u, int32_t* col,
+                            double* e_out, int32_t* row_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = tk[i], u = tv[i];
+        const int64_t pos = rowptr[r] + (i - lowptr[r]);
+        col[pos] = lo[u];
+        if (e_out) e_out[pos] = e_u[u];
+        if (row_out) row_out[pos] = (int32_t)r;
+    }
+}
+
+// Upper part (including the self-loop): pair u after the row's lower part.
+__global__ void k_place_up(const int32_t* lo, const int32_t* hi, int64_t nu, const int64_t* rowptr,
+                           const int64_t* lowptr, const int64_t* upptr, const double* e_u, int32_t* col,
+                           double* e_out, int32_t* row_out) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = lo[u];
+        const int64_t pos = rowptr[r] + (lowptr[r + 1] - lowptr[r]) + (u - upptr[r]);
+        col[pos] = hi[u];
+        if (e_out) e_out[pos] = e_u[u];
+        if (row_out) row_out[pos] = (int32_t)r;
+    }
+}
+
+// Unweighted graphs without repeated pairs: deg_a is the row length.
+__global__ void k_degree_len(const int64_t* rowptr, int64_t n, double* deg, float* inv_deg,
+                             unsigned long long* max_len) {
+    unsigned long long mx = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = rowptr[r + 1] - rowptr[r];
+        const double s = (double)l;
+        deg[r] = s;
+        inv_deg[r] = s > 0.0 ? __fdiv_rn(1.0f, __double2float_rn(s)) : 0.0f;
+        mx = max(mx, (unsigned long long)l);
+    }
+    warp_max_out(max_len, mx);
+}
+
 }  // namespace
 
 void graph_release(cleora_ctx* ctx) {
@@ -512,13 +600,17 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     // 2. entry keys (and weights)
     const int bits = bit_width(n);  // n < 2^bits, so the all-ones key is never a real entry
     const uint64_t invalid = (bits * 2 >= 64) ? ~0ull : ((1ull << (2 * bits)) - 1ull);
+    // undirected: one (min, max) key per edge while pair indices fit 32 bits
+    const bool sym = !directed && E < ((int64_t)1 << 31);
+    const int mode = directed ? KEYS_DIRECTED : (sym ? KEYS_SYM : KEYS_PAIR);
+    const int64_t mk = sym ? E : m;  // keys emitted
     DBuf<float> va(ctx), vb(ctx);
     if (w) {
-        CL_TRY(va.alloc((size_t)m));
-        CL_TRY(vb.alloc((size_t)m));
+        CL_TRY(va.alloc((size_t)mk));
+        CL_TRY(vb.alloc((size_t)mk));
     }
     if (E > 0) {
-        k_entries<<<grid_for(E, 256, sms), 256, 0, s>>>(src, dst, w, E, directed, rank_tab.p, rank_mask, n,
+        k_entries<<<grid_for(E, 256, sms), 256, 0, s>>>(src, dst, w, E, mode, rank_tab.p, rank_mask, n,
                                                        has_empty, bits, invalid, ka, w ? va.p : nullptr, d_flag);
         CL_LAUNCHED(ctx);
         int missing = 0;
@@ -529,6 +621,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
     rank_tab.reset();
 
     g.directed = directed != 0;
+    if (sym) return csr_undirected(ctx, ka, kb, w ? va.p : nullptr, w ? vb.p : nullptr, E, 2 * E, n, bits, g);
     return csr_from_entries(ctx, ka, kb, w ? va.p : nullptr, w ? vb.p : nullptr, m, 2 * E, n, bits,
                             invalid, g);
 }
@@ -626,6 +719,158 @@ int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float*
         CL_TRY(dalloc(ctx, &g.val, (size_t)(nnz ? nnz : 1)));
         k_values<<<grid_for(nnz, 256, sms), 256, 0, s>>>(rows.p, weighted ? e.p : nullptr, start, scal.p + 3,
                                                          g.deg, nnz, g.val);
+        CL_LAUNCHED(ctx);
+    }
+    CL_CUDA(ctx, cudaStreamSynchronize(s));
+    g.built = true;
+    return CLEORA_OK;
+}
+
+int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* vbuf_a, float* vbuf_b, int64_t E,
+                   int64_t kbuf_words, int64_t n, int bits, Graph& g) {
+    cudaStream_t s = ctx->stream;
+    const int sms = ctx->num_sms;
+    const bool weighted = vbuf_a != nullptr;
+    DBuf<int64_t> scal(ctx);  // device scalars: [0] count, [1] flag, [2] max_len, [3] m_valid
+    CL_TRY(scal.alloc(4));
+    CL_CUDA(ctx, cudaMemsetAsync(scal.p, 0, 4 * sizeof(int64_t), s));
+    int* d_flag = reinterpret_cast<int*>(scal.p + 1);
+    const int64_t m_valid = E;  // no key is dropped
+
+    // 1. stable sort of the (lo, hi) keys (weights carried along): duplicates stay in edge order
+    uint64_t* keys = nullptr;
+    float* vals = nullptr;
+    {
+        cub::DoubleBuffer<uint64_t> dk(kbuf_a, kbuf_b);
+        size_t tb = 0;
+        DBuf<unsigned char> tmp(ctx);
+        if (weighted) {
+            cub::DoubleBuffer<float> dv(vbuf_a, vbuf_b);
+            CL_CUDA(ctx, cub::DeviceRadixSort::SortPairs(nullptr, tb, dk, dv, E, 0, 2 * bits, s));
+            CL_TRY(tmp.alloc(tb));
+            CL_CUDA(ctx, cub::DeviceRadixSort::SortPairs(tmp.p, tb, dk, dv, E, 0, 2 * bits, s));
+            vals = dv.Current();
+        } else {
+            CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(nullptr, tb, dk, E, 0, 2 * bits, s));
+            CL_TRY(tmp.alloc(tb));
+            CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(tmp.p, tb, dk, E, 0, 2 * bits, s));
+        }
+        keys = dk.Current();
+    }
+    uint64_t* spare = (keys == kbuf_a) ? kbuf_b : kbuf_a;
+
+    // 2. unique pairs: run starts (head flags and starts share the spare key buffer)
+    uint8_t* head = reinterpret_cast<uint8_t*>(spare);
+    int64_t* start = reinterpret_cast<int64_t*>(spare) + (E + 7) / 8;
+    DBuf<int64_t> starts_buf(ctx);
+    if ((E + 7) / 8 + E > kbuf_words) {
+        CL_TRY(starts_buf.alloc((size_t)E));
+        start = starts_buf.p;
+    }
+    k_heads<<<grid_for(E, 256, sms), 256, 0, s>>>(keys, E, ~0ull, head);
+    CL_LAUNCHED(ctx);
+    {
+        size_t tb = 0;
+        thrust::counting_iterator<int64_t> it(0);
+        CL_CUDA(ctx, cub::DeviceSelect::Flagged(nullptr, tb, it, head, start, scal.p, E, s));
+        DBuf<unsigned char> tmp(ctx);
+        CL_TRY(tmp.alloc(tb));
+        CL_CUDA(ctx, cub::DeviceSelect::Flagged(tmp.p, tb, it, head, start, scal.p, E, s));
+    }
+    CL_CUDA(ctx, cudaMemcpyAsync(scal.p + 3, &m_valid, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    int64_t nu = 0;
+    CL_CUDA(ctx, cudaMemcpyAsync(&nu, scal.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, cudaStreamSynchronize(s));
+
+    // 3. per pair: lo, hi, e (FP64 weight sum in edge order; unweighted: the multiplicity)
+    DBuf<int32_t> plo(ctx), phi(ctx);
+    DBuf<double> pe(ctx);
+    CL_TRY(plo.alloc((size_t)nu));
+    CL_TRY(phi.alloc((size_t)nu));
+    if (weighted) CL_TRY(pe.alloc((size_t)nu));
+    k_runs<<<grid_for(nu, 256, sms), 256, 0, s>>>(keys, vals, start, nu, scal.p + 3, bits, phi.p, plo.p,
+                                                  weighted ? pe.p : nullptr, d_flag);
+    CL_LAUNCHED(ctx);
+    int flag = 0;
+    CL_CUDA(ctx, cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, cudaStreamSynchronize(s));
+    const bool not_unit = flag != 0;
+    const bool has_val = weighted || not_unit;
+    if (!weighted && not_unit) {
+        CL_TRY(pe.alloc((size_t)nu));
+        k_counts_to_e<<<grid_for(nu, 256, sms), 256, 0, s>>>(start, nu, m_valid, pe.p);
+        CL_LAUNCHED(ctx);
+    }
+
+    // 4. transposed half: pairs sorted stably by hi (the key buffers are free now)
+    uint32_t* tk = reinterpret_cast<uint32_t*>(kbuf_a);
+    uint32_t* tv = tk + nu;
+    uint32_t* tk2 = tv + nu;
+    uint32_t* tv2 = tk2 + nu;  // 16 nu bytes <= 16 E bytes of kbuf_a
+    int64_t nt = 0;
+    k_transpose_keys<<<grid_for(nu, 256, sms), 256, 0, s>>>(plo.p, phi.p, nu, (uint32_t)n, tk, tv);
+    CL_LAUNCHED(ctx);
+    {
+        cub::DoubleBuffer<uint32_t> dk(tk, tk2), dv(tv, tv2);
+        size_t tb = 0;
+        CL_CUDA(ctx, cub::DeviceRadixSort::SortPairs(nullptr, tb, dk, dv, nu, 0, bits, s));
+        DBuf<unsigned char> tmp(ctx);
+        CL_TRY(tmp.alloc(tb));
+        CL_CUDA(ctx, cub::DeviceRadixSort::SortPairs(tmp.p, tb, dk, dv, nu, 0, bits, s));
+        tk = dk.Current();
+        tv = dv.Current();
+    }
+    k_count_below<<<1, 1, 0, s>>>(tk, nu, (uint32_t)n, scal.p);
+    CL_LAUNCHED(ctx);
+    CL_CUDA(ctx, cudaMemcpyAsync(&nt, scal.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, cudaStreamSynchronize(s));
+    const int64_t nnz = nu + nt;
+    g.nnz = nnz;
+
+    // 5. rowptr = (pairs with lo = r before) + (pairs with hi = r before)
+    DBuf<int64_t> upptr(ctx), lowptr(ctx);
+    CL_TRY(upptr.alloc((size_t)(n + 1)));
+    CL_TRY(lowptr.alloc((size_t)(n + 1)));
+    k_rowptr<<<grid_for(nu + 1, 256, sms), 256, 0, s>>>(plo.p, nu, n, upptr.p);
+    k_rowptr<<<grid_for(nt + 1, 256, sms), 256, 0, s>>>(reinterpret_cast<const int32_t*>(tk), nt, n, lowptr.p);
+    CL_LAUNCHED(ctx);
+    CL_TRY(dalloc(ctx, &g.rowptr, (size_t)(n + 1)));
+    k_add_rowptr<<<grid_for(n + 1, 256, sms), 256, 0, s>>>(upptr.p, lowptr.p, n, g.rowptr);
+    CL_LAUNCHED(ctx);
+
+    // 6. place both parts
+    CL_TRY(dalloc(ctx, &g.col, (size_t)(nnz ? nnz : 1)));
+    DBuf<double> e(ctx);
+    DBuf<int32_t> rows(ctx);
+    if (has_val) {
+        CL_TRY(e.alloc((size_t)nnz));
+        CL_TRY(rows.alloc((size_t)nnz));
+    }
+    k_place_low<<<grid_for(nt, 256, sms), 256, 0, s>>>(tk, tv, nt, g.rowptr, lowptr.p, plo.p, pe.p, g.col,
+                                                       has_val ? e.p : nullptr, has_val ? rows.p : nullptr);
+    k_place_up<<<grid_for(nu, 256, sms), 256, 0, s>>>(plo.p, phi.p, nu, g.rowptr, lowptr.p, upptr.p, pe.p, g.col,
+                                                      has_val ? e.p : nullptr, has_val ? rows.p : nullptr);
+    CL_LAUNCHED(ctx);
+
+    // 7. degrees (weighted or repeated pairs: FP64 row sums in ascending column order)
+    CL_TRY(dalloc(ctx, &g.deg, (size_t)(n ? n : 1)));
+    CL_TRY(dalloc(ctx, &g.inv_deg, (size_t)(n ? n : 1)));
+    unsigned long long* d_max = reinterpret_cast<unsigned long long*>(scal.p + 2);
+    if (has_val)
+        k_degree<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, e.p, n, g.deg, g.inv_deg, d_max);
+    else
+        k_degree_len<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, n, g.deg, g.inv_deg, d_max);
+    CL_LAUNCHED(ctx);
+    int64_t max_len = 0;
+    CL_CUDA(ctx, cudaMemcpyAsync(&max_len, scal.p + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, cudaStreamSynchronize(s));
+    g.max_row_len = max_len;
+    g.has_val = has_val;
+
+    // 8. stored values
+    if (has_val) {
+        CL_TRY(dalloc(ctx, &g.val, (size_t)(nnz ? nnz : 1)));
+        k_values<<<grid_for(nnz, 256, sms), 256, 0, s>>>(rows.p, e.p, nullptr, scal.p + 3, g.deg, nnz, g.val);
         CL_LAUNCHED(ctx);
     }
     CL_CUDA(ctx, cudaStreamSynchronize(s));

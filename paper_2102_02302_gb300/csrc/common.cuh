@@ -177,6 +177,9 @@ void graph_release(cleora_ctx* ctx);
 // words each) and weight buffers are consumed as scratch.
 int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* vbuf_a, float* vbuf_b,
                      int64_t m, int64_t kbuf_words, int64_t n, int bits, uint64_t invalid, Graph& g);
+// The same for an undirected graph from one (lo, hi) key per edge (lo <= hi, E < 2^31).
+int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* vbuf_a, float* vbuf_b, int64_t E,
+                   int64_t kbuf_words, int64_t n, int bits, Graph& g);
 int check_weights(cleora_ctx* ctx, const float* w, int64_t E);  // finite and > 0
 int bit_width_of(int64_t v);
 int sort_unique_ids(cleora_ctx* ctx, const uint64_t* keys, int64_t count, uint64_t** ids_out, int64_t* n_out);
