@@ -3,6 +3,8 @@ include/cleora.h declares (no compute call: there is no GPU here)."""
 import os
 import re
 
+import ctypes
+
 import paper_2102_02302_gb300 as pkg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -39,3 +41,37 @@ def test_library_is_built_for_sm_103a_only():
     flags = " ".join(pkg.build_native.ARCH)
     assert "arch=compute_103a,code=sm_103a" in flags
     assert flags.count("-gencode") == 1
+
+
+def _job(E, d=128, storage="f32", directed=False, weighted=False, nodes_hint=0):
+    job = pkg.cleora.cleora_job()
+    job.num_edges = E
+    job.directed = int(directed)
+    job.d = d
+    job.iters = 4
+    job.storage = pkg.cleora.DTYPES[storage]
+    job.nodes_hint = nodes_hint
+    job.weights = 1 if weighted else None  # only its presence is read
+    return job
+
+
+def test_serving_memory_estimate_model():
+    """The admission estimate (host arithmetic, no device): it covers the resident CSR and both
+    embedding buffers, grows with edges, d, FP32 storage and weights, and adds the transient
+    of the hot-first row partition once T is larger than twice the 72 MiB hot-row budget."""
+    est = lambda **kw: pkg.cleora.load().cleora_serve_estimate(ctypes.byref(_job(**kw)))
+    assert pkg.cleora.load().cleora_serve_estimate(None) == -1
+    n, E = 1_000_000, 10_000_000
+    base = est(E=E, nodes_hint=n)
+    m = 2 * E
+    assert base >= m * 8 + 2 * n * 128 * 4  # CSR entries, ping-pong FP32 T
+    assert est(E=2 * E, nodes_hint=n) > base
+    assert est(E=E, nodes_hint=n, d=256) > base
+    assert est(E=E, nodes_hint=n, storage="bf16") < base
+    assert est(E=E, nodes_hint=n, weighted=True) > base
+    assert est(E=E, nodes_hint=n, directed=True) < base
+    # T of 100k x 128 BF16 (25.6 MB) fits twice in the hot budget: no partition term; at
+    # 2M nodes (512 MB) the partition's copy of the column array is counted
+    small_t = est(E=E, nodes_hint=100_000, storage="bf16")
+    big_t = est(E=E, nodes_hint=2_000_000, storage="bf16")
+    assert big_t - small_t > m * 4
