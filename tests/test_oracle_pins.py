@@ -167,6 +167,60 @@ def test_duplicate_edge_equals_one_edge_of_double_weight():
     assert np.array_equal(ga.dense_m(), gb.dense_m())
 
 
+def _rn32(x):
+    """The float32 nearest to the rational x, ties to even: one rounding of the exact
+    value (float(x) is within one float32 step of it; the three neighbours are compared
+    exactly)."""
+    from fractions import Fraction
+    c = np.float32(float(x))
+    best = None
+    for cand in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        key = (abs(Fraction(float(cand)) - x), int(np.array(cand).view(np.uint32)) & 1)
+        if best is None or key < best[0]:
+            best = (key, cand)
+    return best[1]
+
+
+def test_stored_fp32_values_round_the_exact_transition_probabilities_once():
+    # The compact store of M (Sec. 3.2: M_ab = e_ab / deg(v_a); the builder keeps FP32
+    # values) rounds the exact ratio once, val = fp32(e_ab / deg_a), and keeps
+    # inv_deg = 1.0f / fp32(deg_a) (IEEE division, correctly rounded).  Expected values come
+    # from exact rationals of a hand-built adjacency, not from the oracle's own arithmetic.
+    # The weights make the tempting variants differ: fp32(e)/fp32(deg) for the values and
+    # fp32(1/deg) for the inverse degree.
+    from fractions import Fraction
+    w = [0.7, 0.1, 1.1, 0.1, 0.05, 1.0, 0.3, 2.9, 2.9]
+    src = [0, 0, 0, 0, 0, 1, 1, 2, 2]
+    dst = [1, 2, 2, 3, 3, 0, 0, 2, 1]
+    e = synth.from_index_pairs(src, dst, True, weights=w)
+    g = oracle.build_from(e)
+    ids = synth.node_ids(4, 0)
+    pos = {int(x): i for i, x in enumerate(g.ids)}
+    adj = {}
+    for s, t, wk in zip(src, dst, np.asarray(w, np.float32)):
+        key = (pos[int(ids[s])], pos[int(ids[t])])
+        adj[key] = adj.get(key, Fraction(0)) + Fraction(float(wk))
+    assert g.has_val
+    split_val = split_inv = False
+    for a in range(g.n):
+        row = {b: x for (r, b), x in adj.items() if r == a}
+        deg = sum(row.values(), Fraction(0))
+        if deg == 0:
+            assert g.inv_deg32[a] == 0.0 and g.rowptr[a] == g.rowptr[a + 1]
+            continue
+        assert sum((x / deg for x in row.values()), Fraction(0)) == 1  # row-stochastic
+        deg32 = np.float32(float(deg))
+        want_inv = _rn32(Fraction(1) / Fraction(float(deg32)))
+        assert g.inv_deg32[a].view(np.uint32) == want_inv.view(np.uint32)
+        split_inv |= want_inv != _rn32(Fraction(1) / deg)
+        for k in range(g.rowptr[a], g.rowptr[a + 1]):
+            b = int(g.col[k])
+            want = _rn32(row[b] / deg)
+            assert g.val32[k].view(np.uint32) == want.view(np.uint32), (a, b)
+            split_val |= want != np.float32(np.float32(float(row[b])) / deg32)
+    assert split_val and split_inv  # the graph tells the rounding rules apart
+
+
 @pytest.mark.parametrize("c", [4.0, 3.0, 0.125])
 def test_scaling_all_weights_leaves_m_unchanged(c):
     e = synth.random_multigraph(30, 120, 5, True, True)
