@@ -331,7 +331,11 @@ void cleora_serve_destroy(cleora_server* s);
  * Inputs, all device pointers owned by the caller: the CSR of M (rowptr[n+1] int64,
  * col[nnz] int32, and val[nnz] FP32 M_ab, or val == NULL for unit weights, where rows are
  * summed and the normalisation removes the common 1/deg factor), T_in (n x d, storage type)
- * and the output T_out (n x d, same type, must not overlap T_in).  Results agree with
+ * and the output T_out (n x d, same type).  The CSR must be well formed: rowptr[0] = 0,
+ * non-decreasing, rowptr[n] = nnz (entries past nnz are not read; a row reaching past it is
+ * wrong).  Alignment: T_in and T_out on 16-byte boundaries (the kernel moves 16-byte
+ * vectors), rowptr on 8, col and val on 4; T_in and T_out must not overlap.  A call that
+ * breaks either rule returns CLEORA_ERR_INVALID_ARG before launching anything.  Results agree with
  * cleora_propagate within the parity tolerances (1e-5 FP32, 2e-2 BF16); the summation order
  * can differ because rows longer than split_len are split differently.
  *

@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(256) k_propagate_noalloc(prop::Args a, unsigne
     View v = view_of(scratch);
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
+    // ok_split is false only when the split table overflowed (the host bound excludes it);
+    // long rows then run whole on the warp path instead of being left out
     const bool ok_split = v.hdr->overflow == 0;
     const int64_t nchunks = ok_split ? v.hdr->nchunks : 0;
     const int64_t nblocks = (a.n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
@@ -129,7 +131,8 @@ __global__ void __launch_bounds__(256) k_propagate_noalloc(prop::Args a, unsigne
         } else {
             const int64_t rb = ((int64_t)t - nchunks) * ROWS_PER_BLOCK;
             const int64_t re = min(a.n, rb + ROWS_PER_BLOCK);
-            K::template rows_coop<true>(a, rb, re, lane, g, lg);
+            if (ok_split) K::template rows_coop<true>(a, rb, re, lane, g, lg);
+            else K::template rows_coop<false>(a, rb, re, lane, g, lg);
         }
         __syncwarp();
     }
@@ -223,6 +226,15 @@ extern "C" int cleora_propagate_noalloc(const int64_t* rowptr, const int32_t* co
     const int64_t min_len = (2 * nnz + cap - 1) / cap;
     if (split_len == 0) split_len = min_len > 256 ? min_len : 256;
     if (split_len < min_len || split_len < 1) return CLEORA_ERR_INVALID_ARG;
+    // The kernel gathers and stores 16-byte vectors of T and reads rowptr, col and val
+    // with their natural widths: a misaligned view (a tensor slice with a storage offset)
+    // would fault on the device, so it is refused here, before anything is launched.
+    const uintptr_t tin = reinterpret_cast<uintptr_t>(T_in), tout = reinterpret_cast<uintptr_t>(T_out);
+    if (((tin | tout) & 15) || (reinterpret_cast<uintptr_t>(rowptr) & 7) ||
+        (reinterpret_cast<uintptr_t>(col) & 3) || (reinterpret_cast<uintptr_t>(val) & 3))
+        return CLEORA_ERR_INVALID_ARG;
+    const uintptr_t tbytes = (uintptr_t)n * (uintptr_t)d * (storage == CLEORA_F32 ? 4u : 2u);
+    if (tin < tout + tbytes && tout < tin + tbytes) return CLEORA_ERR_INVALID_ARG;  // overlap
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return CLEORA_ERR_CUDA;

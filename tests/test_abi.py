@@ -37,6 +37,21 @@ def test_status_strings_without_a_device():
     assert lib.cleora_status_string(-4) == b"call out of order"
 
 
+def test_noalloc_refuses_misaligned_or_overlapping_buffers_before_any_cuda_call():
+    # The allocation-free step moves 16-byte vectors of T: misaligned (or overlapping) buffers
+    # are refused by host checks that run before any CUDA call, so fake addresses are safe
+    # here; only rejected combinations are passed.
+    lib = pkg.load()
+    f = lambda rp, c, v, tin, tout: lib.cleora_propagate_noalloc(rp, c, v, 4, 10, tin, tout, 8, 0, 0, None)
+    assert f(0x10000, 0x20000, None, 0x30004, 0x40000) == pkg.CLEORA_ERR_INVALID_ARG  # T_in
+    assert f(0x10000, 0x20000, None, 0x30000, 0x40008) == pkg.CLEORA_ERR_INVALID_ARG  # T_out
+    assert f(0x10004, 0x20000, None, 0x30000, 0x40000) == pkg.CLEORA_ERR_INVALID_ARG  # rowptr
+    assert f(0x10000, 0x20002, None, 0x30000, 0x40000) == pkg.CLEORA_ERR_INVALID_ARG  # col
+    assert f(0x10000, 0x20000, 0x50001, 0x30000, 0x40000) == pkg.CLEORA_ERR_INVALID_ARG  # val
+    assert f(0x10000, 0x20000, None, 0x30000, 0x30010) == pkg.CLEORA_ERR_INVALID_ARG  # overlap
+    assert f(0x10000, 0x20000, None, 0x30000, None) == pkg.CLEORA_ERR_INVALID_ARG
+
+
 def test_library_is_built_for_sm_103a_only():
     flags = " ".join(pkg.build_native.ARCH)
     assert "arch=compute_103a,code=sm_103a" in flags

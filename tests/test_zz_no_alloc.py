@@ -1,15 +1,18 @@
-"""The allocation-free propagation step against the regular entry point (GPU).
+"""The allocation-free propagation step against the regular entry point and the oracle (GPU).
 
 cleora_propagate_noalloc exists for callers that may not let the library allocate device
 memory (a framework allocator that owns all of HBM, a latency-critical loop that cannot pay
 for cudaMalloc/cudaFree, a job that must not fail with out-of-memory halfway).  Here the
 test owns every buffer: it reads the CSR and T_0 from a regular context, then runs two
-allocation-free steps in a row and compares each with cleora_propagate's own iterations,
-within the parity tolerances.  This file is collected last on purpose.
+allocation-free steps in a row and compares each with cleora_propagate's own iterations and
+with the FP64 oracle, within the parity tolerances.  It also checks that the calls take no
+device memory and that misaligned or overlapping buffers are refused before any launch.
+This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -20,6 +23,12 @@ BF16_TOL = 2e-2
 
 def _bf16_to_f32(bits):
     return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+def _bf16_round(x):
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint32)
+    return (r << 16).view(np.float32).astype(np.float64)
 
 
 CASES = [
@@ -67,21 +76,76 @@ def test_noalloc_two_steps_match_propagate(name, d, storage, split_len):
             want.append(ctx.embeddings(storage))
     torch.cuda.synchronize()
 
+    g = oracle.build_from(e)
+    T0o = oracle.init(g.ids, d, 5)
+    if storage == "bf16":
+        T0o = _bf16_round(T0o)
+    oracle_want = [oracle.propagate(g, T0o, k) for k in (1, 2)]
+
     T1 = torch.empty_like(T0)
     T2 = torch.empty_like(T0)
     pkg.cleora_propagate_noalloc(rowptr, col, val, n, nnz, T0, T1, d, storage, split_len)
     pkg.cleora_propagate_noalloc(rowptr, col, val, n, nnz, T1, T2, d, storage, split_len)
     torch.cuda.synchronize()
-    for got_t, ref in zip((T1, T2), want):
+    for got_t, ref, ow in zip((T1, T2), want, oracle_want):
         got = got_t.cpu().numpy()
         if storage == "f32":
-            err = np.abs(got.astype(np.float64) - ref.astype(np.float64)).max()
-            assert err <= F32_TOL, err
+            gf = got.astype(np.float64)
+            assert np.abs(gf - ref.astype(np.float64)).max() <= F32_TOL
+            assert np.abs(gf - ow).max() <= F32_TOL
         else:
-            g = _bf16_to_f32(got.view(np.uint16)).astype(np.float64)
+            gf = _bf16_to_f32(got.view(np.uint16)).astype(np.float64)
             r = _bf16_to_f32(ref).astype(np.float64)
-            assert np.abs(g - r).max() <= BF16_TOL
-        assert np.isfinite(got.astype(np.float64)).all()
+            assert np.abs(gf - r).max() <= BF16_TOL
+            assert np.abs(gf - ow).max() <= BF16_TOL
+            cos = (gf * ow).sum(1) / (np.linalg.norm(gf, axis=1) * np.linalg.norm(ow, axis=1))
+            assert cos.min() >= 0.999
+        assert np.isfinite(gf).all()
+
+
+def test_noalloc_takes_no_device_memory_and_refuses_bad_views():
+    import torch
+    import paper_2102_02302_gb300 as pkg
+
+    e = synth.star(20000, seed=3)
+    d = 64
+    with pkg.Context(0) as ctx:
+        ctx.graph_build(e.src, e.dst, e.weights, e.directed)
+        info = ctx.info()
+        n, nnz = info["n"], info["nnz"]
+        rowptr = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(nnz, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        pkg.cleora_get_csr(ctx.handle, rowptr, col)
+        ctx.init(d, 1, "bf16")
+        T0 = torch.empty((n, d), dtype=torch.int16, device="cuda")
+        pkg.cleora_get_embeddings(ctx.handle, T0, "bf16")
+        ctx.sync()
+    torch.cuda.synchronize()
+    T1 = torch.empty_like(T0)
+    # the first call on the device looks up the scratch array and loads the kernels
+    pkg.cleora_propagate_noalloc(rowptr, col, None, n, nnz, T0, T1, d, "bf16", 256)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        pkg.cleora_propagate_noalloc(rowptr, col, None, n, nnz, T0, T1, d, "bf16", 256)
+        pkg.cleora_propagate_noalloc(rowptr, col, None, n, nnz, T1, T0, d, "bf16", 256)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+    # a view 8 bytes into T (BF16, 4 elements) is not 16-byte aligned; overlapping input and
+    # output buffers are refused as well; nothing is launched for either
+    flat = T0.view(-1)
+    shifted = flat[4:4 + (n - 1) * d].view(n - 1, d)
+    out = torch.empty((n - 1, d), dtype=torch.int16, device="cuda")
+    with pytest.raises(pkg.CleoraError) as ex:
+        pkg.cleora_propagate_noalloc(rowptr, col, None, n - 1, nnz, shifted, out, d, "bf16", 256)
+    assert ex.value.status == pkg.CLEORA_ERR_INVALID_ARG
+    with pytest.raises(pkg.CleoraError) as ex:
+        pkg.cleora_propagate_noalloc(rowptr, col, None, n, nnz, T0, T0, d, "bf16", 256)
+    assert ex.value.status == pkg.CLEORA_ERR_INVALID_ARG
+    torch.cuda.synchronize()
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
