@@ -79,6 +79,9 @@ def _load():
         lib.oracle_propagate.restype = ctypes.c_int
         lib.oracle_step_rows.argtypes = [_P, ctypes.c_int, _P, _P, _I64, _P, ctypes.c_int]
         lib.oracle_step_rows.restype = ctypes.c_int
+        lib.oracle_step_csr_rows.argtypes = [_P, _P, _P, _I64, ctypes.c_int, _P, _P, _I64, _P,
+                                             ctypes.c_int]
+        lib.oracle_step_csr_rows.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -185,6 +188,26 @@ def step_rows(g: Graph, T_prev, rows, nthreads: int = 0) -> np.ndarray:
                                   _ptr(rows), rows.shape[0], _ptr(out), nthreads)
     if rc != 0:
         raise OracleError(f"oracle_step_rows failed ({rc})")
+    return out
+
+
+def step_csr_rows(rowptr, col, e, T_prev_f32, rows, nthreads: int = 0) -> np.ndarray:
+    """One iteration on the listed rows of a graph given as a CSR (e = None: unit e_ab), from
+    an FP32 previous iterate: rownorm(sum_b (e_ab / deg_a) T_prev[b]) in FP64.  For graphs
+    too large for the oracle's own build; the CSR must come from a checked source."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    e = None if e is None else np.ascontiguousarray(e, dtype=np.float64)
+    T = np.ascontiguousarray(T_prev_f32, dtype=np.float32)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    n = rowptr.shape[0] - 1
+    if T.shape[0] != n:
+        raise ValueError("T_prev must have one row per node")
+    out = np.empty((rows.shape[0], T.shape[1]), np.float64)
+    rc = _load().oracle_step_csr_rows(_ptr(rowptr), _ptr(col), _ptr(e), n, T.shape[1], _ptr(T),
+                                      _ptr(rows), rows.shape[0], _ptr(out), nthreads)
+    if rc != 0:
+        raise OracleError(f"oracle_step_csr_rows failed ({rc})")
     return out
 
 

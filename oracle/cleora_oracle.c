@@ -271,3 +271,73 @@ int oracle_step_rows(const oracle_graph* g, int d, const double* T_prev, const i
         if (rows[r] < 0 || rows[r] >= g->n) return -1;
     return run_rows(g, d, T_prev, out, rows, nrows, nthreads);
 }
+
+/* ---- one step over an external CSR (graphs too large to build here) ---------------------- */
+
+typedef struct {
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* e;
+    int64_t n;
+    int d;
+    const float* T;
+    const int64_t* rows;
+    int64_t nrows;
+    double* out;
+    int64_t next; /* next row to hand out (atomic) */
+    int bad;
+} csr_job;
+
+static void csr_row(const csr_job* jb, int64_t a, double* y) {
+    const int d = jb->d;
+    int64_t beg = jb->rowptr[a], end = jb->rowptr[a + 1];
+    if (beg == end) {
+        for (int j = 0; j < d; ++j) y[j] = (double)jb->T[a * (int64_t)d + j];
+    } else {
+        double deg = 0.0;
+        for (int64_t k = beg; k < end; ++k) deg += jb->e ? jb->e[k] : 1.0;
+        for (int j = 0; j < d; ++j) y[j] = 0.0;
+        for (int64_t k = beg; k < end; ++k) {
+            double mab = (jb->e ? jb->e[k] : 1.0) / deg;
+            const float* tb = jb->T + (int64_t)jb->col[k] * d;
+            for (int j = 0; j < d; ++j) y[j] += mab * (double)tb[j];
+        }
+    }
+    double ss = 0.0;
+    for (int j = 0; j < d; ++j) ss += y[j] * y[j];
+    double nrm = sqrt(ss);
+    for (int j = 0; j < d; ++j) y[j] = nrm > 0.0 ? y[j] / nrm : 0.0;
+}
+
+static void* csr_worker(void* arg) {
+    csr_job* jb = (csr_job*)arg;
+    for (;;) {
+        int64_t r = __atomic_fetch_add(&jb->next, 1, __ATOMIC_RELAXED);
+        if (r >= jb->nrows) break;
+        csr_row(jb, jb->rows[r], jb->out + r * (int64_t)jb->d);
+    }
+    return NULL;
+}
+
+int oracle_step_csr_rows(const int64_t* rowptr, const int32_t* col, const double* e, int64_t n,
+                         int d, const float* T_prev, const int64_t* rows, int64_t nrows,
+                         double* out, int nthreads) {
+    if (!rowptr || !T_prev || !rows || !out || d < 1 || n < 0 || nrows < 0) return -1;
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t a = rows[r];
+        if (a < 0 || a >= n) return -1;
+        for (int64_t k = rowptr[a]; k < rowptr[a + 1]; ++k)
+            if (col[k] < 0 || col[k] >= n) return -1;
+    }
+    csr_job jb = {rowptr, col, e, n, d, T_prev, rows, nrows, out, 0, 0};
+    if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    int started = 1;
+    for (int t = 1; t < nthreads; ++t, ++started)
+        if (pthread_create(&th[t], NULL, csr_worker, &jb) != 0) break;
+    csr_worker(&jb);
+    for (int t = 1; t < started; ++t) pthread_join(th[t], NULL);
+    return 0;
+}

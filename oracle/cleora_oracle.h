@@ -49,6 +49,14 @@ int oracle_propagate(const oracle_graph* g, int d, const double* T_in, int iters
 /* One iteration restricted to the listed rows: out[r] = rownorm(M T_prev)[rows[r]]. */
 int oracle_step_rows(const oracle_graph* g, int d, const double* T_prev, const int64_t* rows,
                      int64_t nrows, double* out, int nthreads);
+/* The same step for a graph given as a CSR (rowptr[n+1], col[nnz]; e[nnz] = e_ab, or NULL
+ * when every e_ab is 1) and an FP32 T_prev (n x d), for graphs too large to build here:
+ * out[r] = rownorm(sum_b (e_ab / deg_a) T_prev[b]) for a = rows[r], deg_a = sum_b e_ab in
+ * ascending position, FP64 throughout; a row without entries keeps T_prev[a] renormalised.
+ * Rows are handed to threads one at a time (long rows do not hold up a block of others). */
+int oracle_step_csr_rows(const int64_t* rowptr, const int32_t* col, const double* e, int64_t n,
+                         int d, const float* T_prev, const int64_t* rows, int64_t nrows,
+                         double* out, int nthreads);
 
 #ifdef __cplusplus
 }

@@ -5,10 +5,11 @@ CSR, FP32 and BF16 results are compared entry by entry.
 
 Large undirected graph (41M nodes, 1.4B edges, 2.8B CSR entries, d = 128): the oracle cannot
 run whole on the host, so the checks are properties that hold at any size (every id present,
-CSR invariants, symmetry, unit norms, determinism) and the relation that defines an
-iteration, T_k[a] = rownorm(sum_b M_ab T_{k-1}[b]), on sampled rows (the largest hubs and
-random rows): the oracle rebuilds those rows of M from the edge list alone and applies one
-step to the previous iterate.
+CSR invariants, symmetry, unit norms, determinism), the CSR rows of a sample compared bit for
+bit with the oracle's own build of the edges that touch them, and the relation that defines an
+iteration, T_k[a] = rownorm(sum_b M_ab T_{k-1}[b]), on over a million rows that include every
+row the kernel splits across warps: the oracle applies one FP64 step to the library's
+previous iterate over the checked CSR.
 """
 import numpy as np
 import pytest
@@ -68,6 +69,24 @@ def large():
     torch.cuda.empty_cache()
 
 
+SPLIT_LEN = 8192  # the library's default: longer rows run as split chunks
+
+
+def _id_key(x):
+    """uint64 ids held in int64 tensors -> keys whose signed order is the unsigned order."""
+    import torch
+    return x ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=x.device)
+
+
+def _segments(rowptr, rows):
+    """Entry positions of the given rows, concatenated in the given order."""
+    import torch
+    beg, end = rowptr[rows], rowptr[rows + 1]
+    lens = end - beg
+    start = torch.repeat_interleave(beg - torch.cumsum(lens, 0) + lens, lens)
+    return start + torch.arange(int(lens.sum()), device=rowptr.device), lens
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_large_graph_properties_and_sampled_step(large, storage):
     import torch
@@ -88,13 +107,11 @@ def test_large_graph_properties_and_sampled_step(large, storage):
         pkg.cleora_node_ids(ctx.handle, ids)
         pkg.cleora_get_csr(ctx.handle, rowptr, col, None, None, deg)
         ctx.sync()
-        # ids: strictly ascending as unsigned (flipping the sign bit maps unsigned order to
-        # signed order), and every endpoint is one of them
-        sign = torch.tensor(-(1 << 63), dtype=torch.int64, device=dev)
-        flip = ids ^ sign
+        # ids: strictly ascending as unsigned, and every endpoint is one of them
+        flip = _id_key(ids)
         assert bool((flip[1:] > flip[:-1]).all())
         for ends in (src, dst):
-            f = ends ^ sign
+            f = _id_key(ends)
             pos = torch.searchsorted(flip, f).clamp_(max=n - 1)
             assert bool((flip[pos] == f).all())
             del f, pos
@@ -104,19 +121,48 @@ def test_large_graph_properties_and_sampled_step(large, storage):
         assert bool((deg == lens.to(torch.float64)).all())
         assert int(col.min()) >= 0 and int(col.max()) < n
         assert int(lens.max()) == inf["max_row_len"] and inf["max_row_len"] > 2_000_000
-        # sampled rows: the largest hubs and random rows
         gen = torch.Generator(device="cpu").manual_seed(7)
+        long_rows = torch.nonzero(lens > SPLIT_LEN).flatten().cpu()
+        assert long_rows.numel() > 1000
+        rnd = torch.randint(0, n, (1_000_000,), generator=gen)
         hubs = torch.topk(lens, 6).indices.cpu()
-        rnd = torch.randint(0, n, (8000,), generator=gen)
-        rows = torch.unique(torch.cat([hubs, rnd]))
         rp = rowptr.cpu()
-        for r in rows[:2000].tolist():  # ascending, no duplicates, symmetric
+        for r in torch.unique(torch.cat([hubs, rnd[:2000]])).tolist():  # ascending, symmetric
             seg = col[int(rp[r]):int(rp[r + 1])].long()
             assert bool((seg[1:] > seg[:-1]).all())
             if seg.numel() and seg.numel() < 5000:
                 back = seg[torch.randint(0, seg.numel(), (1,), generator=gen).item()].item()
                 bseg = col[int(rp[back]):int(rp[back + 1])]
                 assert bool((bseg == r).any())
+
+        # CSR rows of a sample, bit for bit against the oracle's build of every edge that
+        # touches them (that build holds each sampled row whole): neighbour ids and degrees
+        sub = torch.unique(torch.cat([hubs, rnd[:100_000],
+                                      long_rows[torch.randperm(long_rows.numel(), generator=gen)[:64]]]))
+        s_ids = ids[sub.to(dev)]
+        s_sorted = torch.sort(_id_key(s_ids)).values
+
+        def member(x):
+            f = _id_key(x)
+            p = torch.searchsorted(s_sorted, f).clamp_(max=s_sorted.numel() - 1)
+            return s_sorted[p] == f
+
+        mask = member(src) | member(dst)
+        sg = oracle.build_graph(src[mask].cpu().numpy().view(np.uint64),
+                                dst[mask].cpu().numpy().view(np.uint64), None, False)
+        del mask
+        sg_key = _id_key(torch.from_numpy(sg.ids.view(np.int64)))
+        pa = torch.searchsorted(sg_key, _id_key(s_ids.cpu()))  # sampled rows in sg
+        assert bool((sg_key[pa] == _id_key(s_ids.cpu())).all())
+        lib_pos, lib_len = _segments(rowptr, sub.to(dev))
+        lib_nbr = ids[col[lib_pos].long()].cpu().numpy().view(np.uint64)
+        sg_pos, sg_len = _segments(torch.from_numpy(sg.rowptr), pa)
+        sg_nbr = sg.ids[sg.col[sg_pos.numpy()]]
+        assert torch.equal(lib_len.cpu(), sg_len)
+        assert np.array_equal(lib_nbr, sg_nbr)
+        assert np.array_equal(deg[sub.to(dev)].cpu().numpy(), sg.deg[pa.numpy()])
+        del lib_pos, lib_nbr, sg, sg_pos, sg_nbr
+
         # iterations: deterministic, unit norms
         d = spec.d
         ctx.init(d, 0, storage)
@@ -134,28 +180,21 @@ def test_large_graph_properties_and_sampled_step(large, storage):
         norms = torch.linalg.vector_norm(T4, dim=1)
         tol_norm = 1e-5 if storage == "f32" else 1e-2
         assert float((norms - 1).abs().max()) <= tol_norm
-        # one step on the sampled rows, with M rebuilt by the oracle from the edge list
-        s_ids = ids[rows.to(dev)]
-        s_sorted = torch.sort(s_ids ^ sign).values
 
-        def member(x):
-            f = x ^ sign
-            p = torch.searchsorted(s_sorted, f).clamp_(max=s_sorted.numel() - 1)
-            return s_sorted[p] == f
-
-        mask = member(src) | member(dst)
-        sub_src = src[mask].cpu().numpy().view(np.uint64)
-        sub_dst = dst[mask].cpu().numpy().view(np.uint64)
-        del mask
-        sg = oracle.build_graph(sub_src, sub_dst, None, False)
-        flip_cpu = flip.cpu()
-        sg_flip = torch.from_numpy(sg.ids.view(np.int64)) ^ torch.tensor(-(1 << 63), dtype=torch.int64)
-        full_pos = torch.searchsorted(flip_cpu, sg_flip)  # sub-graph node -> full row
-        T_prev = T3[full_pos.to(dev)].cpu().numpy().astype(np.float64)
-        s_flip = s_ids.cpu() ^ torch.tensor(-(1 << 63), dtype=torch.int64)
-        sub_rows = torch.searchsorted(sg_flip, s_flip).numpy()
-        want = oracle.step_rows(sg, T_prev, sub_rows)
+        # one step on >= 1M rows including every split row: the oracle's FP64 step over the
+        # checked CSR from the library's previous iterate (BF16 values are exact in FP32)
+        rows = torch.unique(torch.cat([long_rows, rnd]))
+        assert rows.numel() >= 1_000_000
         got = T4[rows.to(dev)].cpu().numpy().astype(np.float64)
+        del T4
+        T_prev = T3.cpu().numpy()
+        del T3
+        col_h = col.cpu().numpy()
+        want = oracle.step_csr_rows(rp.numpy(), col_h, None, T_prev, rows.numpy())
+        del T_prev, col_h
         tol = 1e-5 if storage == "f32" else 2e-2
         assert np.abs(got - want).max() <= tol
+        if storage == "bf16":
+            cos = (got * want).sum(1) / (np.linalg.norm(got, axis=1) * np.linalg.norm(want, axis=1))
+            assert cos.min() >= 0.999
     torch.cuda.set_stream(torch.cuda.default_stream())

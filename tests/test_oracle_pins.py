@@ -397,6 +397,23 @@ def test_sink_keeps_its_row_renormalised_and_step_rows_agrees():
     np.testing.assert_array_equal(oracle.step_rows(g, T0, rows), T1[rows])
 
 
+@pytest.mark.parametrize("weighted,directed", [(False, False), (True, True), (False, True)])
+def test_step_over_an_external_csr_equals_the_oracle_step(weighted, directed):
+    # The one-step routine for graphs too large to build here takes the CSR from outside;
+    # fed the oracle's own CSR (and an FP32-exact previous iterate) it must reproduce the
+    # oracle's step bit for bit, sinks and duplicate edges included.
+    e = synth.random_multigraph(200, 1500, 4, directed, weighted)
+    g = oracle.build_from(e)
+    T = oracle.init(g.ids, 24, 3)  # exact in FP32
+    rows = np.array([0, g.n - 1, 5, 17, 5, 100], np.int64)
+    want = oracle.step_rows(g, T, rows)
+    ev = g.e if g.has_val else None
+    got = oracle.step_csr_rows(g.rowptr, g.col, ev, T.astype(np.float32), rows)
+    assert np.array_equal(got, want)
+    with pytest.raises(oracle.OracleError):
+        oracle.step_csr_rows(g.rowptr, g.col, ev, T.astype(np.float32), np.array([g.n]))
+
+
 def test_power_law_small_case_sanity():
     e = synth.SMALL.generate()
     g = oracle.build_from(e)
