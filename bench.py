@@ -86,33 +86,45 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ["paper_2102_02302_gb300/csrc/propagate_kernels.cuh",
-                  "paper_2102_02302_gb300/csrc/propagate.cu",
-                  "paper_2102_02302_gb300/csrc/prop_f32_v16.cu", "paper_2102_02302_gb300/csrc/prop_f32_v8.cu",
-                  "paper_2102_02302_gb300/csrc/prop_bf16_v16.cu", "paper_2102_02302_gb300/csrc/prop_bf16_v8.cu"]
+PROP_SOURCES = ["paper_2102_02302_gb300/csrc/propagate_kernels.cuh",
+                "paper_2102_02302_gb300/csrc/propagate.cu",
+                "paper_2102_02302_gb300/csrc/prop_f32_v16.cu", "paper_2102_02302_gb300/csrc/prop_f32_v8.cu",
+                "paper_2102_02302_gb300/csrc/prop_bf16_v16.cu", "paper_2102_02302_gb300/csrc/prop_bf16_v8.cu"]
+BATCH_SOURCES = PROP_SOURCES + ["paper_2102_02302_gb300/csrc/batch_kernels.cuh",
+                                "paper_2102_02302_gb300/csrc/batch.cu",
+                                "paper_2102_02302_gb300/csrc/batch_f32_v16.cu",
+                                "paper_2102_02302_gb300/csrc/batch_f32_v8.cu",
+                                "paper_2102_02302_gb300/csrc/batch_bf16_v16.cu",
+                                "paper_2102_02302_gb300/csrc/batch_bf16_v8.cu"]
 
 
-def kernel_source_sha():
+def source_sha(files):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    for f in files:
+        p = os.path.join(ROOT, f)
+        if os.path.exists(p):
+            with open(p, "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload, storage):
-    """DRAM bytes per propagate launch from the committed ncu summary, or None when the
-    kernel sources changed since it was taken."""
+def kernel_source_sha():
+    return source_sha(PROP_SOURCES)
+
+
+def measured_traffic(key, files=None):
+    """DRAM bytes (read + write) per launch (per replay for the batch) from the committed
+    ncu summary profiles/traffic.json, or None when the sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
-    if t.get("source_sha") != kernel_source_sha():
+    e = t.get("entries", {}).get(key)
+    if e is None or e.get("source_sha") != source_sha(files or PROP_SOURCES):
         return None
-    e = t.get(workload, {}).get(storage)
-    return None if e is None else e["dram_bytes_per_launch"]
+    return e["dram_bytes"]
 
 
 def model_bytes(n, nnz, d, es, has_val):
@@ -124,6 +136,35 @@ def model_bytes(n, nnz, d, es, has_val):
 def compulsory_bytes(n, nnz, d, es, has_val):
     """Lower bound with perfect reuse: CSR once, T read once, T written once."""
     return 8 * (n + 1) + 4 * nnz + (4 * nnz if has_val else 0) + 2 * es * d * n
+
+
+def roofline_block(n, nnz, d, es, hv, iter_s, traffic, peak, peak_kind, kernel):
+    """Roofline of one propagate launch (one iteration).  `achieved` and `frac` are read on
+    DRAM bytes from ncu (dram__bytes_read + write per launch) over the CUDA-event time; the
+    byte model (CSR once, one gathered row per entry, T written once) and the compulsory
+    bytes (T read once) are reported beside it.  Without a DRAM capture of the current kernel
+    build the model figure stands in and `basis` says so."""
+    mb = model_bytes(n, nnz, d, es, hv)
+    cb = compulsory_bytes(n, nnz, d, es, hv)
+    model_gbs, comp_gbs = mb / iter_s / 1e9, cb / iter_s / 1e9
+    if traffic is not None:
+        achieved, basis = traffic / iter_s / 1e9, "dram bytes (ncu) / CUDA-event time"
+    else:
+        achieved, basis = model_gbs, "byte model (no DRAM capture of this kernel build)"
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "basis": basis, "kernel": kernel,
+            "launch_ms": iter_s * 1e3,
+            "model_bytes": mb, "model_gbs": model_gbs, "model_frac": model_gbs / peak,
+            "compulsory_bytes": cb, "compulsory_frac": comp_gbs / peak,
+            "bytes_model": "8(n+1) + 4nnz (+4nnz values) + s*d*nnz gathered + s*d*n written",
+            "peak_kind": f"{peak_kind} copy bandwidth (frac of {peak_kind})",
+            "kernel_sha": kernel_source_sha()}
+
+
+def prop_kernel_name(st, d):
+    es = 4 if st == "f32" else 2
+    vec = 16 if d * es // 16 >= 32 else 8
+    return f"k_propagate<{'float' if st == 'f32' else '__nv_bfloat16'}, {vec}, ...>"
 
 
 class ClockSampler:
@@ -200,7 +241,7 @@ def cpu_baseline(workload):
     spec, g, T0 = oracle_sample_setup(workload)
     rate, dt = oracle_iteration_rate(spec, g, T0, 1)
     cores = os.cpu_count() or 1
-    return {"value": rate, "unit": "nnz*d/s per iteration", "cores": cores, "kind": "oracle",
+    return {"value": rate, "unit": "nnz*d/s", "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, one propagation iteration of {spec.name} "
                       f"(n={g.n}, nnz={g.nnz}, d={spec.d}; same generator family as the "
                       f"workload, smaller), {dt:.2f} s on {cores} threads"}
@@ -387,7 +428,7 @@ def generate_batch(count=4096, seed=0, workers=None):
     return specs, edges
 
 
-def batch_measure(device, steps, warmup, count=4096):
+def batch_measure(device, steps, warmup, count=4096, peak=None, peak_kind="measured"):
     import torch
     import paper_2102_02302_gb300 as pkg
     t = time.perf_counter()
@@ -402,10 +443,13 @@ def batch_measure(device, steps, warmup, count=4096):
         del descs, edges
         tot = b.totals
         work = 0
+        mbytes = 0  # byte model of one replay (every graph is weighted: per-entry values)
         sched = {}
         for g, sp in enumerate(specs):
             inf = b.info(g)
             work += inf["nnz"] * sp.d * sp.iters
+            mbytes += sp.iters * model_bytes(inf["n"], inf["nnz"], sp.d, 2, True)
+            mbytes += (2 + 2 + 4) * sp.d * inf["n"]  # T_0 written; last T read, FP32 out written
             sched.setdefault(f"bf16_d{sp.d}", b.schedule(g))
         for _ in range(warmup):
             b.run(None)
@@ -423,8 +467,23 @@ def batch_measure(device, steps, warmup, count=4096):
         torch.cuda.nvtx.range_pop()
         run_ms = float(np.median(times))
         launches = b.launches()
+    replay_s = run_ms * 1e-3
+    traffic = measured_traffic("batch/bf16", BATCH_SOURCES)
+    if peak is None:
+        peak, peak_kind = measured_peaks()
+    model_gbs = mbytes / replay_s / 1e9
+    achieved = model_gbs if traffic is None else traffic / replay_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "basis": ("byte model (no DRAM capture of this kernel build)" if traffic is None
+                      else "dram bytes (ncu) of one replay / CUDA-event replay time"),
+            "model_bytes": mbytes, "model_gbs": model_gbs, "model_frac": model_gbs / peak,
+            "bytes_model": "sum over graphs of I * (8(n+1) + 8nnz + 2*d*nnz + 2*d*n) + 8*d*n (init, output)",
+            "peak_kind": f"{peak_kind} copy bandwidth (frac of {peak_kind})",
+            "kernel_sha": source_sha(BATCH_SOURCES)}
     return {"graphs": count, "storage": "bf16", "nodes": tot["nodes"], "nnz": tot["nnz"],
-            "nnz_d_iters": work, "value": work / (run_ms * 1e-3), "unit": "nnz*d/s per iteration",
+            "roofline": roof,
+            "nnz_d_iters": work, "value": work / (run_ms * 1e-3), "unit": "nnz*d/s",
             "run_ms": run_ms, "launches_per_run": launches, "max_iters": tot["max_iters"],
             "schedules": sched, "generate_s": gen_s, "create_s": create_s,
             "value_def": "sum over graphs of nnz*d*I / CUDA-graph replay time (init, all steps, FP32 output)"}
@@ -592,6 +651,95 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
                        "d in {64,128,256,1024}, I in {3,4,5}, FP32/BF16 50/50"}
 
 
+def cpu_baseline_blocks(pkg, ctx, info, spec, target_entries=800_000_000, start_frac=1 / 3):
+    """The FP64 oracle timed on host cores over a contiguous block of rows of the workload's
+    own graph (rows are in ascending-id order, and ids are unrelated to degree, so a block is
+    a random sample of rows), from its FP32 T_0: one step of `oracle.step_csr_rows`.  The
+    rate (entries * d / time) is extrapolated to the whole graph."""
+    import torch
+    import oracle
+    n, nnz, d = info["n"], info["nnz"], spec.d
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rowptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    pkg.cleora_get_csr(ctx.handle, rowptr, col)
+    ctx.init(d, 0, "f32")
+    T0 = torch.empty((n, d), dtype=torch.float32, device=dev)
+    pkg.cleora_get_embeddings(ctx.handle, T0, "f32")
+    ctx.sync()
+    r0 = int(n * start_frac)
+    k0 = int(rowptr[r0])
+    r1 = int(torch.searchsorted(rowptr, torch.tensor([k0 + min(target_entries, nnz - k0)], device=dev)))
+    r1 = max(r0 + 1, min(r1, n))
+    k1 = int(rowptr[r1])
+    col_blk = col[k0:k1].cpu().numpy()
+    del col
+    # full-length rowptr whose rows outside the block are empty; block rows index col_blk
+    rp = (rowptr - k0).clamp_(0, k1 - k0).cpu().numpy()
+    del rowptr
+    T_host = T0.cpu().numpy()
+    del T0
+    rows = np.arange(r0, r1, dtype=np.int64)
+    t = time.perf_counter()
+    oracle.step_csr_rows(rp, col_blk, None, T_host, rows)
+    dt = time.perf_counter() - t
+    del T_host, col_blk, rp
+    cores = os.cpu_count() or 1
+    rate = (k1 - k0) * d / dt
+    return {"value": rate, "unit": "nnz*d/s", "cores": cores, "kind": "oracle",
+            "sample": f"extrapolated: one FP64 oracle step (step_csr_rows) over rows [{r0}, {r1}) "
+                      f"of the full graph ({r1 - r0} rows, {k1 - k0} of its {nnz} CSR entries, "
+                      f"d = {d}, from the FP32 T_0), {dt:.1f} s on {cores} threads; the rate per "
+                      f"entry is taken to hold for all entries",
+            "seconds": dt, "entries": k1 - k0}
+
+
+def config_leg(key, spec, device, steps, warmup, peak, peak_kind):
+    """A smaller workload: GPU per-iteration time for FP32 and BF16 storage (build + init +
+    I iterations per step, CUDA events on the context's stream) beside a full, timed FP64
+    oracle run of all I iterations on the host cores (its graph build is not timed)."""
+    import torch
+    import oracle
+    import paper_2102_02302_gb300 as pkg
+    e = spec.generate()
+    dev = torch.device("cuda", device)
+    src = torch.from_numpy(e.src.view(np.int64)).to(dev)
+    dst = torch.from_numpy(e.dst.view(np.int64)).to(dev)
+    w = None if e.weights is None else torch.from_numpy(e.weights).to(dev)
+    stream = torch.cuda.Stream(device)
+    prev = torch.cuda.current_stream(device)
+    torch.cuda.set_stream(stream)
+    out = {"workload": spec.name, "d": spec.d, "iters": spec.iters}
+    with pkg.Context(device, stream.cuda_stream) as ctx:
+        ctx.graph_build(src, dst, w, spec.directed)
+        info = ctx.info()
+        n, nnz, hv = info["n"], info["nnz"], info["has_val"]
+        out.update({"n": n, "nnz": nnz, "weighted": hv, "directed": spec.directed})
+        for st in ("f32", "bf16"):
+            r = time_dtype(pkg, ctx, (src, dst, w, None), spec, st, steps, warmup)
+            it = float(np.median(r["iter_ms"])) * 1e-3
+            es = 4 if st == "f32" else 2
+            out[st] = {"value": nnz * spec.d / it, "unit": "nnz*d/s", "iter_ms": it * 1e3,
+                       "step_ms": float(np.mean(r["step_ms"])),
+                       "roofline": roofline_block(n, nnz, spec.d, es, hv, it,
+                                                  measured_traffic(f"{key}/{st}"), peak,
+                                                  peak_kind, prop_kernel_name(st, spec.d))}
+    torch.cuda.set_stream(prev)
+    del src, dst, w
+    torch.cuda.empty_cache()
+    g = oracle.build_from(e)
+    T0 = oracle.init(g.ids, spec.d, 0)
+    t = time.perf_counter()
+    oracle.propagate(g, T0, spec.iters)
+    dt = time.perf_counter() - t
+    cores = os.cpu_count() or 1
+    out["oracle"] = {"value": g.nnz * spec.d * spec.iters / dt, "unit": "nnz*d/s",
+                     "run_s": dt, "cores": cores, "kind": "oracle",
+                     "sample": f"full FP64 oracle run, all {spec.iters} iterations of the whole graph"}
+    out["bf16_speedup_over_f32"] = out["f32"]["iter_ms"] / out["bf16"]["iter_ms"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -607,6 +755,8 @@ def main():
                     help="L2 bytes kept for hot rows (0: library default, 1: off)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 10k-node and 2M-node workloads (GPU and full oracle runs)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--batch-count", type=int, default=4096)
     args = ap.parse_args()
@@ -663,6 +813,7 @@ def main():
     torch.cuda.set_stream(stream)
     storages = ["bf16", "f32"] if args.storage == "both" else [args.storage]
     results = {}
+    cpu = None
     with pkg.Context(device, stream.cuda_stream) as ctx:
         if args.hot_bytes:
             ctx.set_option("hot_bytes", args.hot_bytes)
@@ -679,6 +830,11 @@ def main():
             r["max_step_ms"], r["max_iter_ms"] = max_over_ranks(
                 [np.mean(r["step_ms"]), np.median(r["iter_ms"])], "cuda")
             results[st] = r
+        if not args.no_cpu and rank == 0 and world == 1:
+            if args.workload in ("large", "large_1_40"):
+                cpu = cpu_baseline_blocks(pkg, ctx, info, spec)
+            else:
+                cpu = cpu_baseline(args.workload)
 
     n, nnz, d, hv = info["n"], info["nnz"], spec.d, info["has_val"]
     peak, peak_kind = measured_peaks()
@@ -703,6 +859,9 @@ def main():
             "launches": r["launches"],
             "clocks": r["clocks"],
             "wall_s": r["wall_s"],
+            "roofline": roofline_block(n, nnz, d, es, hv, t_iter,
+                                       measured_traffic(f"{args.workload}/{st}"), peak, peak_kind,
+                                       prop_kernel_name(st, d)),
         }
 
     sums = {st: summary(st) for st in storages}
@@ -715,24 +874,26 @@ def main():
         torch.cuda.empty_cache()
         t_e2e, h2d, d2h, split = e2e_measure(pkg, spec, e2e_host, e2e_out, head, args.e2e_steps, device)
         del e2e_host, e2e_out  # 43 GB of pinned host memory, not needed by the later parts
-        e2e = {"value": world * nnz * d * spec.iters / t_e2e, "unit": "nnz*d/s per iteration",
+        e2e = {"value": world * nnz * d * spec.iters / t_e2e, "unit": "nnz*d/s",
                "s_per_step": t_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "phases": split,
+               "value_def": f"nnz*d*I / end-to-end step time (I = {spec.iters})",
                "note": "public C ABI with pinned host buffers: edge upload, build, init, "
                        f"{spec.iters} iterations and FP32 result download per step"}
 
     batched = None
     if not args.no_batch:
-        batched = batch_measure(device, args.steps, args.warmup, args.batch_count)
+        batched = batch_measure(device, args.steps, args.warmup, args.batch_count, peak, peak_kind)
         batched["value"] *= world
 
     serving = None
     if not args.no_serve:
         serving = serve_measure(device, args.serve_jobs)
 
-    cpu = None
-    if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline(args.workload)
+    configs = None
+    if not args.no_configs and rank == 0 and world == 1:
+        configs = {k: config_leg(k, WORKLOADS[k], device, args.steps, args.warmup, peak, peak_kind)
+                   for k in ("small", "mid")}
 
     line = {
         "metric": "nnz*d/s per iteration", "value": hs["value"], "unit": "nnz*d/s",
@@ -748,22 +909,17 @@ def main():
                    "value_def": "nnz*d / median per-iteration time (CUDA events)",
                    "hot_bytes": args.hot_bytes or "default",
                    "generator_s": gen_s},
-        "roofline": {"bound": "hbm", "achieved": hs["model_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": hs["model_gbs"] / peak, "traffic": measured_traffic(args.workload, head),
-                     "traffic_gbs": (None if measured_traffic(args.workload, head) is None else
-                                     measured_traffic(args.workload, head) / (hs["iter_ms_median"] * 1e-3) / 1e9),
-                     "kernel_sha": kernel_source_sha(),
-                     "peak_kind": f"{peak_kind} copy bandwidth",
-                     "bytes_model": "8(n+1) + 4nnz (+4nnz values) + s*d*nnz gathered + s*d*n written",
-                     "compulsory_gbs": hs["compulsory_gbs"],
-                     "compulsory_frac": hs["compulsory_gbs"] / peak},
+        "roofline": hs["roofline"],
+        "roofline_f32": sums["f32"]["roofline"] if "f32" in sums else None,
         "gpu_launches": hs["launches"],
         "clocks": hs["clocks"],
         "e2e": e2e,
         "cpu_baseline": cpu,
         "batched": batched,
         "serving": serving,
-        "breakdown": {st: {k: v for k, v in s.items() if k not in ("clocks",)} for st, s in sums.items()},
+        "configs": configs,
+        "breakdown": {st: {k: v for k, v in s.items() if k not in ("clocks", "roofline")}
+                      for st, s in sums.items()},
     }
     if "bf16" in sums and "f32" in sums:
         line["bf16_speedup_over_f32"] = sums["f32"]["iter_ms_median"] / sums["bf16"]["iter_ms_median"]
