@@ -753,6 +753,9 @@ def main():
     ap.add_argument("--storage", default="both", choices=["both", "bf16", "f32"])
     ap.add_argument("--hot-bytes", type=int, default=0,
                     help="L2 bytes kept for hot rows (0: library default, 1: off)")
+    ap.add_argument("--staging", type=int, default=0,
+                    help="gathered rows reach the sums through 0: automatic, 1: registers, 2: the shared-memory ring")
+    ap.add_argument("--ring-stages", type=int, default=0, help="ring stages (0: library default)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
@@ -817,6 +820,10 @@ def main():
     with pkg.Context(device, stream.cuda_stream) as ctx:
         if args.hot_bytes:
             ctx.set_option("hot_bytes", args.hot_bytes)
+        if args.staging:
+            ctx.set_option("staging", args.staging)
+        if args.ring_stages:
+            ctx.set_option("ring_stages", args.ring_stages)
         ctx.graph_build(*edges[:3], spec.directed)
         info = ctx.info()
         for st in storages:
@@ -908,6 +915,8 @@ def main():
                    "step": "graph build + init + I iterations on device-resident edges",
                    "value_def": "nnz*d / median per-iteration time (CUDA events)",
                    "hot_bytes": args.hot_bytes or "default",
+                   "staging": {0: "automatic", 1: "registers", 2: "ring"}[args.staging],
+                   "ring_stages": args.ring_stages or "default",
                    "generator_s": gen_s},
         "roofline": hs["roofline"],
         "roofline_f32": sums["f32"]["roofline"] if "f32" in sums else None,

@@ -144,11 +144,29 @@ typedef enum {
                                     twice this; 0 = 72 MiB, 1 = off.  Only the summation
                                     order changes; cleora_get_csr still returns each row
                                     in ascending column order                              */
-    CLEORA_OPT_ID_SLOTS = 6      /* slots of the hash set that collects the distinct ids in
+    CLEORA_OPT_ID_SLOTS = 6,     /* slots of the hash set that collects the distinct ids in
                                     cleora_graph_build; 0 = four times a HyperLogLog
                                     estimate of their number.  A set that fills up is
                                     rebuilt with 4 x num_edges slots, so any value gives the
                                     same graph                                             */
+    CLEORA_OPT_STAGING = 7,      /* how gathered rows reach the sums: 0 automatic (the ring
+                                    when the shape allows it and T is larger than twice the
+                                    hot-row budget), 1 = registers, 2 = a shared-memory ring
+                                    filled by bulk copies (rows of 32 x 8 or 32 x 16 bytes:
+                                    FP32 d = 64 or 128, BF16 d = 128 or 256; other shapes use
+                                    registers).  With the ring, rows keep ascending column
+                                    order and hot entries are marked in a bitmap instead of
+                                    moved to the front.  Results differ from the register
+                                    path only in summation order                           */
+    CLEORA_OPT_RING_STAGES = 8,  /* stages of the ring (windows of 32 entries): 2, 3 or 4;
+                                    0 = 3                                                  */
+    CLEORA_OPT_TEST_RING_WAIT = 9 /* test hook, 0 or 1: in the next ring launches, the first
+                                    window of every warp waits for one row more than it
+                                    copies.  Each ring wait is bounded (0.5 s): the wait runs
+                                    out, the kernel raises its error flag (cleora_sync then
+                                    returns CLEORA_ERR_DEVICE), waits again (bounded) and
+                                    returns, leaving the context usable.  The results of
+                                    that launch are not valid                              */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);

@@ -35,7 +35,8 @@ CLEORA_BF16 = 1
 DTYPES = {"f32": CLEORA_F32, "float32": CLEORA_F32, "bf16": CLEORA_BF16, "bfloat16": CLEORA_BF16}
 
 OPTIONS = {"vec_bytes": 0, "row_mode": 1, "split_len": 2, "task_nnz": 3, "blocks_per_sm": 4,
-           "hot_bytes": 5, "id_slots": 6}
+           "hot_bytes": 5, "id_slots": 6, "staging": 7, "ring_stages": 8,
+           "test_ring_wait": 9}
 
 # Every symbol include/cleora.h declares: name -> (restype, argtypes)
 SIGNATURES = {

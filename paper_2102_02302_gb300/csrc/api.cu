@@ -80,7 +80,8 @@ int check_err_flag(cleora_ctx* ctx) {
     CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (flag) {
         CL_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->stream));
-        return fail(ctx, CLEORA_ERR_DEVICE, "a kernel reported an out-of-range column index");
+        return fail(ctx, CLEORA_ERR_DEVICE, "a kernel reported an error (flags 0x%x: 1 column index out of "
+                    "range, 2 bad task variant, 4 a shared-memory ring wait ran out)", flag);
     }
     return CLEORA_OK;
 }
@@ -480,6 +481,15 @@ int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value) {
         case CLEORA_OPT_ID_SLOTS:
             if (value < 0) return fail(ctx, CLEORA_ERR_INVALID_ARG, "id slots");
             break;
+        case CLEORA_OPT_STAGING:
+            if (value < 0 || value > 2) return fail(ctx, CLEORA_ERR_INVALID_ARG, "staging");
+            break;
+        case CLEORA_OPT_RING_STAGES:
+            if (value != 0 && (value < 2 || value > 4)) return fail(ctx, CLEORA_ERR_INVALID_ARG, "ring stages");
+            break;
+        case CLEORA_OPT_TEST_RING_WAIT:
+            if (value != 0 && value != 1) return fail(ctx, CLEORA_ERR_INVALID_ARG, "test hook");
+            break;
         default:
             return fail(ctx, CLEORA_ERR_INVALID_ARG, "unknown option");
     }
@@ -502,7 +512,7 @@ int cleora_launch_count(const cleora_ctx* ctx, int64_t* launches) {
 int cleora_hot_entries(const cleora_ctx* ctx, int64_t* hot_entries) {
     if (!ctx || !hot_entries) return CLEORA_ERR_INVALID_ARG;
     if (!ctx->g.built) return CLEORA_ERR_STATE;
-    *hot_entries = ctx->g.hot_cnt ? ctx->g.hot_entries : 0;
+    *hot_entries = (ctx->g.hot_cnt || ctx->g.hot_bits) ? ctx->g.hot_entries : 0;
     return CLEORA_OK;
 }
 

@@ -475,6 +475,7 @@ void graph_release(cleora_ctx* ctx) {
     dfree_null(ctx, g.inv_deg);
     dfree_null(ctx, g.deg);
     dfree_null(ctx, g.hot_cnt);
+    dfree_null(ctx, g.hot_bits);
     g = Graph();
 }
 

@@ -44,6 +44,9 @@ struct Graph {
     int64_t part_budget = 0;
     int32_t* hot_cnt = nullptr;  // n: hot entries at the front of each row
     int64_t hot_entries = 0;     // their total
+    // Shared-memory ring kernel: rows keep ascending order and a bitmap marks the entries that
+    // point at hot rows (bit k & 31 of word k >> 5); hot_bits != NULL instead of hot_cnt.
+    uint32_t* hot_bits = nullptr;
     uint64_t* ids = nullptr;
     int64_t* rowptr = nullptr;
     int32_t* col = nullptr;
@@ -61,7 +64,7 @@ struct Shape {
     int chunks = 0; // vectors per row
 };
 
-enum { OPT_COUNT = 7 };
+enum { OPT_COUNT = 10 };
 
 constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
 constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
@@ -87,7 +90,7 @@ struct cleora_ctx {
     int cur = 0;
     int iteration = 0;
 
-    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int* err_flag = nullptr;  // device int, raised by kernels
     int64_t launches = 0;
     int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails
@@ -200,6 +203,11 @@ int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz);
 void plan_release(cleora_ctx* ctx);
 int plan_ensure(cleora_ctx* ctx);
 int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout);
+// Shapes the shared-memory ring kernel covers: a full warp, one vector per lane, rows of
+// 32 x 8 or 32 x 16 bytes.
+inline bool ring_shape(const Shape& sh) { return sh.G == 32 && sh.cpl == 1 && sh.chunks == 32; }
+bool use_ring(const cleora_ctx* ctx);          // the current (d, storage, options) runs the ring
+constexpr int DEFAULT_RING_STAGES = 3;
 int hot_partition(cleora_ctx* ctx);            // partition rows hot-first (after init)
 int hot_restore(cleora_ctx* ctx);              // back to ascending column order
 int col_out(cleora_ctx* ctx, int32_t* col_dev); // column indices in ascending order per row

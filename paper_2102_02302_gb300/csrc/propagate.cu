@@ -8,12 +8,14 @@
 // chunks, then the runs in row order.  The plan is built on the device and depends only on
 // the graph and the two sizes, never on timing, so the summation order of every row is
 // fixed by the graph's shape.
+#include <vector>
+
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_sort.cuh>
 #include <cub/device/device_select.cuh>
 #include <thrust/iterator/counting_iterator.h>
 
-#include "propagate_kernels.cuh"
+#include "ring_kernels.cuh"
 
 namespace cleora {
 namespace {
@@ -81,11 +83,11 @@ __global__ void k_plan_fill(const int32_t* brk_rows, int64_t nb, int64_t n, cons
     }
 }
 
-// Quarter-octave bin of a count: 0 for 0, else 1 + floor(4 log2 c), at most 127.
+// Quarter-octave bin of a count: 0 for 0, else 1 + floor(4 log2 c), at most 127 (double log2:
+// non-decreasing in c, so a higher count never lands in a lower bin).
 __device__ __forceinline__ int count_bin(uint32_t c) {
     if (c == 0) return 0;
-    const float l = __log2f((float)c);
-    const int b = 1 + (int)(4.0f * l);
+    const int b = 1 + (int)(4.0 * log2((double)c));
     return b > 127 ? 127 : b;
 }
 
@@ -117,6 +119,41 @@ __global__ void k_bins(const uint32_t* cnt, int64_t n, uint8_t* bin, unsigned lo
     __syncthreads();
     for (int i = threadIdx.x; i < 128; i += blockDim.x)
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+// Count range [lo, hi] of the rows in bin b (atomic min / max).
+__global__ void k_bin_range(const uint32_t* cnt, const uint8_t* bin, int64_t n, int b, unsigned* lohi) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (bin[r] == b) {
+            atomicMin(lohi, cnt[r]);
+            atomicMax(lohi + 1, cnt[r]);
+        }
+}
+
+constexpr int FINE = 4096;  // buckets of the boundary bin's fine histogram
+
+__device__ __forceinline__ int fine_bucket(uint32_t c, uint32_t lo, uint32_t hi) {
+    return (int)(((uint64_t)(c - lo) * FINE) / ((uint64_t)(hi - lo) + 1));
+}
+
+__global__ void k_bin_fine(const uint32_t* cnt, const uint8_t* bin, int64_t n, int b, const unsigned* lohi,
+                           unsigned long long* fine) {
+    const uint32_t lo = lohi[0], hi = lohi[1];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (bin[r] == b) atomicAdd(fine + fine_bucket(cnt[r], lo, hi), 1ull);
+}
+
+// Hot flag per row (in place of its bin): every row of a bin above b, and the rows of bin b
+// whose fine bucket is at least fb (fb > FINE: none of bin b).
+__global__ void k_hot_flags(const uint32_t* cnt, uint8_t* bin, int64_t n, int b, int fb, const unsigned* lohi) {
+    const uint32_t lo = lohi[0], hi = lohi[1];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int x = bin[r];
+        bin[r] = (x > b || (x == b && fb <= FINE && fine_bucket(cnt[r], lo, hi) >= fb)) ? 1 : 0;
+    }
 }
 
 // Hot flags of 32 consecutive entries as one bit word (a warp per word, a lane per entry:
@@ -378,6 +415,12 @@ static int sort_rows(cleora_ctx* ctx, const int32_t* col, const float* val, int3
 
 int hot_restore(cleora_ctx* ctx) {
     Graph& g = ctx->g;
+    if (g.hot_bits) {  // ring layout: rows are in ascending order already
+        dfree_null(ctx, g.hot_bits);
+        g.part_row_bytes = 0;
+        g.part_budget = 0;
+        g.hot_entries = 0;
+    }
     if (!g.hot_cnt) return CLEORA_OK;
     int32_t* col2 = nullptr;
     float* val2 = nullptr;
@@ -404,31 +447,49 @@ int hot_restore(cleora_ctx* ctx) {
     return CLEORA_OK;
 }
 
-// Partitions every row hot-first: the entries that point at the rows with the largest
-// in-degree (as many rows as fit in the hot-row L2 budget at the current row size) move to
-// the front of the row, both parts keeping ascending column order.  The kernel gathers the
-// hot part with an L2 evict_last policy and the rest evict_first, so the rows that most
-// entries share stay in L2 while the long tail streams through; the policy is uniform over
-// each part, so no entry carries a mark.  Graphs whose whole T fits twice in the budget are
-// left as they are (everything is reused anyway).
+// The ring pays off once gathers leave L2: automatic mode takes it for T larger than twice
+// the default hot-row budget (graphs whose T fits in L2 keep the register kernel).
+bool use_ring(const cleora_ctx* ctx) {
+    if (ctx->d == 0) return false;
+    const Shape sh = choose_shape(ctx, ctx->d, ctx->dtype);
+    if (!ring_shape(sh)) return false;
+    const int64_t mode = ctx->opt[CLEORA_OPT_STAGING];
+    if (mode == 1) return false;
+    if (mode == 2) return true;
+    const int64_t row_bytes = (int64_t)ctx->d * (ctx->dtype == CLEORA_F32 ? 4 : 2);
+    return ctx->g.n * row_bytes > 2 * DEFAULT_HOT_BYTES;
+}
+
+// Marks the entries that point at the rows with the largest in-degree, as many rows as fit
+// in the hot-row L2 budget at the current row size (whole quarter-octave bins from the top,
+// then the boundary bin's rows from a 4096-bucket histogram of their exact counts).
+//  * Register kernel: every row is partitioned hot-first (both parts keep ascending column
+//    order); the kernel gathers the hot part with an L2 evict_last policy and the rest
+//    evict_first, the policy uniform over each part, so no entry carries a mark.
+//  * Ring kernel: rows keep ascending order; a bitmap over the entries gives each lane's bulk
+//    copy its policy.
+// Graphs whose whole T fits twice in the budget are left as they are (everything is reused).
 int hot_partition(cleora_ctx* ctx) {
     Graph& g = ctx->g;
     const int64_t row_bytes = (int64_t)ctx->d * (ctx->dtype == CLEORA_F32 ? 4 : 2);
     const int64_t opt = ctx->opt[CLEORA_OPT_HOT_BYTES];
     const int64_t budget = opt == 0 ? DEFAULT_HOT_BYTES : (opt == 1 ? 0 : opt);
-    const bool uses = ctx->dtype == CLEORA_F32 ? prop::Tune<float>::POLICY : prop::Tune<__nv_bfloat16>::POLICY;
+    const bool ring = use_ring(ctx);
+    const bool uses = ring || (ctx->dtype == CLEORA_F32 ? prop::Tune<float>::POLICY : prop::Tune<__nv_bfloat16>::POLICY);
     const bool want = uses && budget > 0 && g.n > 0 && g.nnz > 0 && g.n * row_bytes > 2 * budget;
-    if (!want && !g.hot_cnt) return CLEORA_OK;
-    if (want && g.hot_cnt && g.part_row_bytes == row_bytes && g.part_budget == budget) return CLEORA_OK;
+    if (!want && !g.hot_cnt && !g.hot_bits) return CLEORA_OK;
+    if (want && g.part_row_bytes == row_bytes && g.part_budget == budget &&
+        ((ring && g.hot_bits) || (!ring && g.hot_cnt)))
+        return CLEORA_OK;
     CL_TRY(hot_restore(ctx));
     if (!want) return CLEORA_OK;
     cudaStream_t s = ctx->stream;
     const int sms = ctx->num_sms;
     const int64_t nw = (g.nnz + 31) / 32;
-    int threshold = 128;  // none hot
     uint32_t* cnt = nullptr;
     uint8_t* bin = nullptr;
-    unsigned long long* hist = nullptr;
+    unsigned long long* hist = nullptr;  // 128 bins + FINE buckets
+    unsigned* lohi = nullptr;
     uint32_t* word = nullptr;
     int64_t* wcnt = nullptr;
     int64_t* rowH = nullptr;
@@ -440,8 +501,9 @@ int hot_partition(cleora_ctx* ctx) {
     do {
         if ((rc = dalloc(ctx, &cnt, (size_t)g.n))) break;
         if ((rc = dalloc(ctx, &bin, (size_t)g.n))) break;
-        if ((rc = dalloc(ctx, &hist, 128))) break;
-        cudaError_t e = cudaMemsetAsync(hist, 0, 128 * sizeof(unsigned long long), s);
+        if ((rc = dalloc(ctx, &hist, 128 + FINE))) break;
+        if ((rc = dalloc(ctx, &lohi, 2))) break;
+        cudaError_t e = cudaMemsetAsync(hist, 0, (128 + FINE) * sizeof(unsigned long long), s);
         if (e == cudaSuccess && g.directed) e = cudaMemsetAsync(cnt, 0, g.n * sizeof(uint32_t), s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
         if (g.directed)
@@ -456,25 +518,64 @@ int hot_partition(cleora_ctx* ctx) {
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
         const int64_t rows = budget / row_bytes;
         int64_t acc = 0;
-        for (int b = 127; b >= 1; --b) {  // whole bins, from the hottest down
+        int b = 127;  // whole bins above b are hot; b is the boundary bin
+        for (; b >= 1; --b) {
             if (acc + (int64_t)h[b] > rows) break;
             acc += (int64_t)h[b];
-            threshold = b;
         }
-        if (threshold == 128) break;  // no whole bin fits: leave the rows as they are
+        if (b < 1) b = 0;  // every row with entries fits
+        int fb = FINE + 1;  // bucket threshold inside bin b (none)
+        if (b >= 1 && h[b] > 0 && acc < rows) {
+            const unsigned init[2] = {0xffffffffu, 0u};
+            e = cudaMemcpyAsync(lohi, init, sizeof(init), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
+            k_bin_range<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, bin, g.n, b, lohi);
+            k_bin_fine<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, bin, g.n, b, lohi, hist + 128);
+            ctx->launches += 2;
+            std::vector<unsigned long long> f(FINE);
+            e = cudaMemcpyAsync(f.data(), hist + 128, FINE * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
+            for (int q = FINE - 1; q >= 0; --q) {  // the rows of the top buckets that still fit
+                if (acc + (int64_t)f[q] > rows) break;
+                acc += (int64_t)f[q];
+                fb = q;
+            }
+        }
+        if (acc == 0) break;  // not even one row fits: leave the rows as they are
+        k_hot_flags<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, bin, g.n, b, fb, lohi);
+        ctx->launches++;
         dfree_null(ctx, cnt);
         if ((rc = dalloc(ctx, &word, (size_t)nw))) break;
         if ((rc = dalloc(ctx, &wcnt, (size_t)nw))) break;
-        if ((rc = dalloc(ctx, &rowH, (size_t)(g.n + 1)))) break;
-        if ((rc = dalloc(ctx, &hot_cnt, (size_t)g.n))) break;
-        if ((rc = dalloc(ctx, &col2, (size_t)g.nnz))) break;
-        if (g.has_val && (rc = dalloc(ctx, &val2, (size_t)g.nnz))) break;
-        k_hot_words<<<grid_for(nw * 32, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, threshold, word, wcnt, nw);
+        k_hot_words<<<grid_for(nw * 32, 256, sms), 256, 0, s>>>(g.col, g.nnz, bin, 1, word, wcnt, nw);
         ctx->launches++;
         size_t tb = 0;
         e = cub::DeviceScan::ExclusiveSum(nullptr, tb, wcnt, wcnt, nw, s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
         if ((rc = dalloc_bytes(ctx, &tmp, tb ? tb : 1))) break;
+        if (ring) {  // hot entries = the popcounts of the words (scanned in place)
+            int64_t last_base = 0;
+            uint32_t last_word = 0;
+            e = cub::DeviceScan::ExclusiveSum(tmp, tb, wcnt, wcnt, nw, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&last_base, wcnt + nw - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&last_word, word + nw - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
+            ctx->launches++;
+            g.hot_entries = last_base + __builtin_popcount(last_word);
+            g.hot_bits = word;
+            word = nullptr;
+            g.part_row_bytes = row_bytes;
+            g.part_budget = budget;
+            break;
+        }
+        if ((rc = dalloc(ctx, &rowH, (size_t)(g.n + 1)))) break;
+        if ((rc = dalloc(ctx, &hot_cnt, (size_t)g.n))) break;
+        if ((rc = dalloc(ctx, &col2, (size_t)g.nnz))) break;
+        if (g.has_val && (rc = dalloc(ctx, &val2, (size_t)g.nnz))) break;
         e = cub::DeviceScan::ExclusiveSum(tmp, tb, wcnt, wcnt, nw, s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "scan", __FILE__, __LINE__); break; }
         ctx->launches++;
@@ -505,6 +606,7 @@ int hot_partition(cleora_ctx* ctx) {
     dfree(ctx, cnt);
     dfree(ctx, bin);
     dfree(ctx, hist);
+    dfree(ctx, lohi);
     dfree(ctx, word);
     dfree(ctx, wcnt);
     dfree(ctx, rowH);
@@ -561,6 +663,22 @@ int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
     const int bps = (int)ctx->opt[CLEORA_OPT_BLOCKS_PER_SM];
     cudaError_t e;
     int grid = 0;
+    if (use_ring(ctx) && (reinterpret_cast<uintptr_t>(Tin) & 15) == 0) {
+        a.hot_cnt = nullptr;
+        a.hot_bits = g.hot_bits;
+        a.test_wait_runout = (int)ctx->opt[CLEORA_OPT_TEST_RING_WAIT];
+        const int st = ctx->opt[CLEORA_OPT_RING_STAGES] ? (int)ctx->opt[CLEORA_OPT_RING_STAGES] : DEFAULT_RING_STAGES;
+        if (ctx->dtype == CLEORA_F32)
+            e = sh.vec == 16 ? ring::launch_f32_v16(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid)
+                             : ring::launch_f32_v8(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid);
+        else
+            e = sh.vec == 16 ? ring::launch_bf16_v16(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid)
+                             : ring::launch_bf16_v8(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "propagate launch", __FILE__, __LINE__);
+        return CLEORA_OK;
+    }
+    if (g.hot_bits) return fail(ctx, CLEORA_ERR_STATE, "rows are laid out for the ring kernel");
     if (ctx->dtype == CLEORA_F32)
         e = sh.vec == 16 ? prop::launch_f32_v16(sh, a, g.has_val, bps, ctx->num_sms, ctx->stream, &grid)
                          : prop::launch_f32_v8(sh, a, g.has_val, bps, ctx->num_sms, ctx->stream, &grid);

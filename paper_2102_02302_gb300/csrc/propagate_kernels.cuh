@@ -69,6 +69,10 @@ struct Args {
     // L2 (gathered evict_last), the rest (in descending column order) are gathered
     // evict_first.  NULL: no partition, every gather evict_normal.
     const int32_t* hot_cnt = nullptr;
+    // Hot flags of the entries in place (bit k & 31 of word k >> 5): entries that point at
+    // the rows kept in L2, for the shared-memory ring kernel (rows keep ascending order).
+    const uint32_t* hot_bits = nullptr;
+    int test_wait_runout = 0;  // ring kernel test hook (see CLEORA_OPT_TEST_RING_WAIT)
 };
 
 // L2 policy of a gather: in a partitioned row the hot segment is loaded evict_last and the
@@ -572,6 +576,13 @@ struct Kern {
         Acc acc;
         acc.zero();
         range_coop(a, acc, k0, k1, beg + (a.hot_cnt ? a.hot_cnt[r] : 0), lane, g, lg);
+        split_store_combine(a, t, acc, lane, g, lg);
+    }
+
+    // A split chunk's partial sum (in acc.t) goes to its slot; the warp that finishes the
+    // row's last chunk adds all slots in a fixed order, normalises and writes the row.
+    __device__ static void split_store_combine(const Args& a, const Task& t, Acc& acc, int lane, int g, int lg) {
+        const int64_t r = t.a;
         reduce_groups(acc);
         const int64_t base = a.split_base[t.b];
         float* slot = a.partials + (base + t.c) * (int64_t)a.d;
