@@ -160,13 +160,16 @@ typedef enum {
                                     path only in summation order                           */
     CLEORA_OPT_RING_STAGES = 8,  /* stages of the ring (windows of 32 entries): 2, 3 or 4;
                                     0 = 3                                                  */
-    CLEORA_OPT_TEST_RING_WAIT = 9 /* test hook, 0 or 1: in the next ring launches, the first
+    CLEORA_OPT_TEST_RING_WAIT = 9, /* test hook, 0 or 1: in the next ring launches, the first
                                     window of every warp waits for one row more than it
                                     copies.  Each ring wait is bounded (0.5 s): the wait runs
                                     out, the kernel raises its error flag (cleora_sync then
                                     returns CLEORA_ERR_DEVICE), waits again (bounded) and
                                     returns, leaving the context usable.  The results of
                                     that launch are not valid                              */
+    CLEORA_OPT_CHUNK_BYTES = 10  /* device bytes one chunk of cleora_chunked_embed may use
+                                    when the library picks the chunks; 0 = 80% of the free
+                                    device memory at the call                              */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
@@ -201,14 +204,28 @@ int cleora_inductive(cleora_ctx* ctx, const uint64_t* new_ids, const uint64_t* n
  * its own (its own M_q and T_0 from the same id hash, `iters` iterations, `storage`) and
  * the results are merged: T_v = sum_q w_qv T^q_v with w_qv = occ_q(v) / sum_k occ_k(v), where
  * occ_q(v) counts the endpoints of chunk q's edges equal to v (the paper's node weight, read
- * as an occurrence share; a self-loop counts twice).  Q = 1 is the plain method.  Outputs:
- * out_ids[*num_nodes] (all nodes, ascending id) and out (FP32, out_rows capacity).  The
- * context's graph and embeddings are replaced by the last chunk's. */
+ * as an occurrence share; a self-loop counts twice; counts are exact 64-bit integers and the
+ * ratio is rounded once to FP32).  Q = 1 is the plain method.
+ * num_chunks = 0: the library picks the chunks (the graph may be larger than device memory):
+ * chunk_offsets[0] holds the number of edges E, and Q is the fewest chunks of equal size
+ * (edges floor(E q / Q) .. floor(E (q+1) / Q) - 1) whose estimated device peak, next to
+ * 28 bytes per node, fits CLEORA_OPT_CHUNK_BYTES (0: 80% of the free device memory).
+ * Out of core: edges given in host memory are uploaded one chunk at a time; a first pass
+ * over the chunks collects the node ids and occurrence counts, a second embeds each chunk and
+ * adds its weighted rows straight into `out` -- device memory, or host memory that the call
+ * maps into the device (pinned for the duration of the call when it is not already).  So the
+ * device holds one chunk's graph and embeddings plus the ids and counts, never the whole edge
+ * list or an n x d accumulator.  cleora_chunked_info reports Q and the device peak.
+ * Outputs: out_ids[*num_nodes] (all nodes, ascending id) and out (FP32, out_rows capacity).
+ * The context's graph and embeddings are replaced by the last chunk's. */
 int cleora_chunked_embed(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst,
                          const float* weights, const int64_t* chunk_offsets, int num_chunks,
                          int directed, int d, int iters, uint64_t seed, cleora_dtype storage,
                          int inputs_on_device, uint64_t* out_ids, float* out, int64_t out_rows,
                          int64_t* num_nodes, int out_on_device);
+/* Chunks of the last cleora_chunked_embed call and the high-water mark of the device memory
+ * the library held during it (bytes, from the context's pool). */
+int cleora_chunked_info(const cleora_ctx* ctx, int* chunks, int64_t* peak_device_bytes);
 
 /* ---------------------------------------------------------------------------------------
  * Batched small graphs: many independent graphs in one persistent launch per iteration

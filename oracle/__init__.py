@@ -82,6 +82,10 @@ def _load():
         lib.oracle_step_csr_rows.argtypes = [_P, _P, _P, _I64, ctypes.c_int, _P, _P, _I64, _P,
                                              ctypes.c_int]
         lib.oracle_step_csr_rows.restype = ctypes.c_int
+        lib.oracle_xxh64.argtypes = [_P, _I64, ctypes.c_uint64]
+        lib.oracle_xxh64.restype = ctypes.c_uint64
+        lib.oracle_hash_strings.argtypes = [_P, _P, _I64, ctypes.c_uint64, _P]
+        lib.oracle_hash_strings.restype = None
         _lib = lib
         return lib
 
@@ -277,3 +281,58 @@ def chunked_embed(src, dst, weights, chunk_offsets, directed, d, iters, seed=0):
         v = np.searchsorted(ids, gq.ids)
         acc[v] += (occ_q / occ_all[v])[:, None] * Tq
     return ids, acc
+
+
+# ---- identifiers and hypergraphs (Sec. 4.3; Sec. 3.2 "Hypergraph Expansion") ------------------
+
+def xxh64(data: bytes, seed: int = 0) -> int:
+    """XXH64 of a byte string (xxHash specification), the paper's identifier hash (Sec. 4.3)."""
+    buf = np.frombuffer(bytes(data), dtype=np.uint8) if len(data) else np.zeros(1, np.uint8)
+    return _load().oracle_xxh64(_ptr(buf), len(data), seed & (2**64 - 1))
+
+
+def hash_strings(strings, seed: int = 0) -> np.ndarray:
+    """XXH64 of every string (bytes or str, UTF-8) -> uint64 ids."""
+    enc = [s.encode() if isinstance(s, str) else bytes(s) for s in strings]
+    offsets = np.zeros(len(enc) + 1, np.int64)
+    offsets[1:] = np.cumsum([len(b) for b in enc])
+    blob = np.frombuffer(b"".join(enc) or b"\0", dtype=np.uint8)
+    out = np.empty(len(enc), np.uint64)
+    _load().oracle_hash_strings(_ptr(blob), _ptr(offsets), len(enc), seed & (2**64 - 1), _ptr(out))
+    return out
+
+
+STAR_KEY = 0x5354415253544152  # "STARSTAR": star-node ids when the caller gives none
+
+
+def star_node_id(h: int) -> int:
+    """Id of hyperedge h's star node when none is given: the splitmix64 output function of
+    h ^ STAR_KEY."""
+    return mix(h ^ STAR_KEY)
+
+
+def expand(members, hoff, mode: str, star_ids=None):
+    """Hypergraph expansion (Sec. 3.2): hyperedge h holds members[hoff[h]:hoff[h+1]]; its
+    distinct members in ascending id order u_0 < ... < u_{k-1} give
+      clique: the edges (u_i, u_j) for i < j, in lexicographic (i, j) order, k(k-1)/2 of them;
+      star:   the edges (s_h, u_i) for every i, s_h the star node (star_ids[h] or
+              star_node_id(h)), k of them.
+    Hyperedges follow their order.  Returns (src, dst) uint64 arrays (undirected edges)."""
+    members = np.asarray(members, dtype=np.uint64)
+    hoff = np.asarray(hoff, dtype=np.int64)
+    src, dst = [], []
+    for h in range(hoff.size - 1):
+        u = sorted(set(int(x) for x in members[hoff[h]:hoff[h + 1]]))
+        if mode == "clique":
+            for i in range(len(u)):
+                for j in range(i + 1, len(u)):
+                    src.append(u[i])
+                    dst.append(u[j])
+        elif mode == "star":
+            s = int(star_ids[h]) if star_ids is not None else star_node_id(h)
+            for x in u:
+                src.append(s)
+                dst.append(x)
+        else:
+            raise ValueError(mode)
+    return np.array(src, dtype=np.uint64), np.array(dst, dtype=np.uint64)

@@ -341,3 +341,81 @@ int oracle_step_csr_rows(const int64_t* rowptr, const int32_t* col, const double
     for (int t = 1; t < started; ++t) pthread_join(th[t], NULL);
     return 0;
 }
+
+/* ---- XXH64 (xxHash specification, 64-bit variant) ---------------------------------------- */
+
+static const uint64_t XP1 = 0x9E3779B185EBCA87ULL, XP2 = 0xC2B2AE3D27D4EB4FULL,
+                      XP3 = 0x165667B19E3779F9ULL, XP4 = 0x85EBCA77C2B2AE63ULL,
+                      XP5 = 0x27D4EB2F165667C5ULL;
+
+static uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+/* little-endian reads, byte by byte (no alignment or host byte-order assumption) */
+static uint64_t le64(const uint8_t* p) {
+    uint64_t v = 0;
+    for (int i = 7; i >= 0; --i) v = (v << 8) | p[i];
+    return v;
+}
+static uint64_t le32(const uint8_t* p) {
+    uint64_t v = 0;
+    for (int i = 3; i >= 0; --i) v = (v << 8) | p[i];
+    return v;
+}
+
+static uint64_t xround(uint64_t acc, uint64_t lane) {
+    acc += lane * XP2;
+    acc = rotl64(acc, 31);
+    return acc * XP1;
+}
+
+static uint64_t xmerge(uint64_t acc, uint64_t v) {
+    acc ^= xround(0, v);
+    return acc * XP1 + XP4;
+}
+
+uint64_t oracle_xxh64(const uint8_t* p, int64_t len, uint64_t seed) {
+    int64_t i = 0;
+    uint64_t acc;
+    if (len >= 32) {
+        uint64_t a1 = seed + XP1 + XP2, a2 = seed + XP2, a3 = seed, a4 = seed - XP1;
+        for (; i + 32 <= len; i += 32) {
+            a1 = xround(a1, le64(p + i));
+            a2 = xround(a2, le64(p + i + 8));
+            a3 = xround(a3, le64(p + i + 16));
+            a4 = xround(a4, le64(p + i + 24));
+        }
+        acc = rotl64(a1, 1) + rotl64(a2, 7) + rotl64(a3, 12) + rotl64(a4, 18);
+        acc = xmerge(acc, a1);
+        acc = xmerge(acc, a2);
+        acc = xmerge(acc, a3);
+        acc = xmerge(acc, a4);
+    } else {
+        acc = seed + XP5;
+    }
+    acc += (uint64_t)len;
+    for (; i + 8 <= len; i += 8) {
+        acc ^= xround(0, le64(p + i));
+        acc = rotl64(acc, 27) * XP1 + XP4;
+    }
+    if (i + 4 <= len) {
+        acc ^= le32(p + i) * XP1;
+        acc = rotl64(acc, 23) * XP2 + XP3;
+        i += 4;
+    }
+    for (; i < len; ++i) {
+        acc ^= (uint64_t)p[i] * XP5;
+        acc = rotl64(acc, 11) * XP1;
+    }
+    acc ^= acc >> 33;
+    acc *= XP2;
+    acc ^= acc >> 29;
+    acc *= XP3;
+    acc ^= acc >> 32;
+    return acc;
+}
+
+void oracle_hash_strings(const uint8_t* bytes, const int64_t* offsets, int64_t count, uint64_t seed,
+                         uint64_t* out) {
+    for (int64_t k = 0; k < count; ++k)
+        out[k] = oracle_xxh64(bytes + offsets[k], offsets[k + 1] - offsets[k], seed);
+}

@@ -58,6 +58,13 @@ int oracle_step_csr_rows(const int64_t* rowptr, const int32_t* col, const double
                          int d, const float* T_prev, const int64_t* rows, int64_t nrows,
                          double* out, int nthreads);
 
+/* XXH64 of len bytes (the xxHash specification, 64-bit variant), the hash the paper uses to
+ * turn entity identifiers into a small fixed-width format (Sec. 4.3).  oracle_hash_strings
+ * hashes strings bytes[offsets[i] .. offsets[i+1]) for i < count. */
+uint64_t oracle_xxh64(const uint8_t* p, int64_t len, uint64_t seed);
+void oracle_hash_strings(const uint8_t* bytes, const int64_t* offsets, int64_t count, uint64_t seed,
+                         uint64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ DTYPES = {"f32": CLEORA_F32, "float32": CLEORA_F32, "bf16": CLEORA_BF16, "bfloat
 
 OPTIONS = {"vec_bytes": 0, "row_mode": 1, "split_len": 2, "task_nnz": 3, "blocks_per_sm": 4,
            "hot_bytes": 5, "id_slots": 6, "staging": 7, "ring_stages": 8,
-           "test_ring_wait": 9}
+           "test_ring_wait": 9, "chunk_bytes": 10}
 
 # Every symbol include/cleora.h declares: name -> (restype, argtypes)
 SIGNATURES = {
@@ -67,6 +67,7 @@ SIGNATURES = {
                                             ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_int, _P, _P, _I64, ctypes.POINTER(_I64),
                                             ctypes.c_int]),
+    "cleora_chunked_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)]),
     "cleora_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int]),
     "cleora_batch_destroy": (None, [_P]),
@@ -314,8 +315,10 @@ def cleora_inductive(ctx, new_ids, nbr_ids, weights=None, out_ids=None, out=None
 
 def cleora_chunked_embed(ctx, src, dst, weights, chunk_offsets, directed, d, iters, seed=0,
                          storage="f32", out_ids=None, out=None) -> int:
-    """Algorithm 1 with edge chunks; returns the number of nodes."""
-    offs = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+    """Algorithm 1 with edge chunks; returns the number of nodes.  chunk_offsets None: the
+    library picks the chunks (see cleora_chunked_info)."""
+    auto = chunk_offsets is None
+    offs = np.ascontiguousarray([int(src.shape[0])] if auto else chunk_offsets, dtype=np.int64)
     ps, ds = _ptr(src)
     pd, _ = _ptr(dst)
     pw, _ = _ptr(weights)
@@ -324,11 +327,18 @@ def cleora_chunked_embed(ctx, src, dst, weights, chunk_offsets, directed, d, ite
     nn = _I64()
     st = DTYPES[storage] if isinstance(storage, str) else int(storage)
     rows = 0 if out is None else int(out.shape[0])
-    _check(ctx, load().cleora_chunked_embed(ctx, ps, pd, pw, offs.ctypes.data, len(offs) - 1,
+    _check(ctx, load().cleora_chunked_embed(ctx, ps, pd, pw, offs.ctypes.data, 0 if auto else len(offs) - 1,
                                             int(bool(directed)), int(d), int(iters),
                                             int(seed) & (2**64 - 1), st, ds, pi, po, rows,
                                             ctypes.byref(nn), do or di))
     return nn.value
+
+
+def cleora_chunked_info(ctx) -> dict:
+    q = ctx_int = ctypes.c_int()
+    peak = _I64()
+    _check(ctx, load().cleora_chunked_info(ctx, ctypes.byref(ctx_int), ctypes.byref(peak)))
+    return {"chunks": q.value, "peak_device_bytes": peak.value}
 
 
 # ---- batched small graphs -------------------------------------------------------------

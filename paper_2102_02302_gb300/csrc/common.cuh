@@ -64,7 +64,7 @@ struct Shape {
     int chunks = 0; // vectors per row
 };
 
-enum { OPT_COUNT = 10 };
+enum { OPT_COUNT = 11 };
 
 constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
 constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
@@ -90,7 +90,9 @@ struct cleora_ctx {
     int cur = 0;
     int iteration = 0;
 
-    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int chunks_used = 0;            // cleora_chunked_embed: chunks of the last call
+    int64_t chunk_peak_bytes = 0;   // ... and the pool's high-water mark during it
     int* err_flag = nullptr;  // device int, raised by kernels
     int64_t launches = 0;
     int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails

@@ -49,8 +49,8 @@ struct Layout {
     static constexpr int STAGE = WIN * ROW;               // bytes per stage
     static constexpr int META = meta_slots<S>();
     static constexpr int META_BYTES = META * WIN * (HV ? 12 : 8);  // col, hot word (, value)
-    // per warp: T stages, metadata, S mbarriers; 128-byte multiple
-    static constexpr int WARP_BYTES = ((S * STAGE + META_BYTES + S * 8) + 127) / 128 * 128;
+    // per warp: T stages, metadata, S "full" and S "empty" mbarriers; 128-byte multiple
+    static constexpr int WARP_BYTES = ((S * STAGE + META_BYTES + 2 * S * 8) + 127) / 128 * 128;
 };
 
 // ---- PTX wrappers ----------------------------------------------------------------------
@@ -62,6 +62,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar) {
 }
 __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -102,9 +105,6 @@ template <int N>
 __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 // a += bf16 (low or high half of w), FP32 result, one rounding
 __device__ __forceinline__ float add_lo(float a, uint32_t w) {
     float r;
@@ -131,8 +131,10 @@ struct Ring {
     int32_t* mcol;          // META x WIN
     uint32_t* mword;        // META x WIN
     float* mval;            // META x WIN (HV)
-    uint32_t bar0;          // shared address of stage 0's mbarrier (stage s at bar0 + 8 s)
+    uint32_t bar0;          // shared address of stage 0's "full" mbarrier (stage s at bar0 + 8 s);
+                            // the "empty" ones follow at bar0 + 8 (S + s)
     uint32_t phase = 0;     // bit s: parity of stage s's next completion
+    uint32_t ephase = 0;    // bit s: parity of stage s's next release
     uint32_t pending = 0;   // bit s: stage s holds an issued, unsummed window
     bool dead = false;      // a wait ran out
     uint64_t pol_hot, pol_cold;
@@ -150,7 +152,7 @@ struct Ring {
         if (HV) p += META * WIN * 4;
         bar0 = smem_addr(p);
         if (lane == 0) {
-            for (int s = 0; s < S; ++s) mbar_init(bar0 + 8 * s);
+            for (int s = 0; s < 2 * S; ++s) mbar_init(bar0 + 8 * s);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncwarp();
@@ -213,6 +215,22 @@ struct Ring {
         return true;
     }
 
+    // Stage s has been read by every lane: the release (arrive) / acquire (wait) pair on its
+    // "empty" barrier orders those reads before the async-proxy writes that refill it (the
+    // producer-acquire pattern of TMA pipelines).
+    __device__ __forceinline__ bool release(const prop::Args& a, int s) {
+        __syncwarp();
+        const uint32_t eb = bar0 + 8 * (S + s);
+        if (lane == 0) mbar_arrive(eb);
+        const bool ok = mbar_wait(eb, (ephase >> s) & 1u);
+        ephase ^= 1u << s;
+        if (!ok) {
+            if (lane == 0) atomicOr(a.err, ERR_WAIT);
+            dead = true;
+        }
+        return ok;
+    }
+
     // Before leaving after a failed wait: wait (bounded) for every stage still in flight.
     __device__ void drain() {
         for (int s = 0; s < S; ++s)
@@ -259,8 +277,7 @@ struct Ring {
             const int64_t kb = K0 + (int64_t)m * WIN;
             cons.window(*this, m % S, m, kb, min(K1, kb + WIN));
             if (m + S < nwin) {
-                __syncwarp();        // every lane has read the stage
-                fence_async_smem();  // ... before the async proxy overwrites it
+                if (!release(a, m % S)) return;
                 issue(a, K0, K1, m + S);
             }
         }

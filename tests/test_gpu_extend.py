@@ -137,3 +137,63 @@ def test_chunked_single_chunk_equals_plain_run_on_gpu():
         pkg.cleora_chunked_embed(ctx.handle, e.src, e.dst, e.weights, [0, e.num_edges], True, 32, 4, 2,
                                  "f32", None, out)
     assert np.array_equal(out, plain)  # weight 1 for every node
+
+
+@pytest.fixture(scope="module")
+def dense_multigraph():
+    # 100k nodes, 20M undirected edges (duplicates kept): the edge list and CSR dominate the
+    # footprint, so a chunk of the edges fits where the whole graph does not
+    return synth.random_multigraph(100_000, 20_000_000, 21, False, False)
+
+
+@pytest.mark.parametrize("storage,out_on", [("f32", "host"), ("f32", "device"), ("bf16", "pinned")])
+def test_chunked_embedding_out_of_core_under_a_device_cap(dense_multigraph, storage, out_on):
+    import torch
+    import paper_2102_02302_gb300 as pkg
+    e = dense_multigraph
+    E, d, iters = e.num_edges, 8, 3
+    g_ids = np.unique(np.concatenate([e.src, e.dst]))
+    n = g_ids.size
+    es = 4 if storage == "f32" else 2
+    whole_csr_t = 8 * (n + 1) + 4 * 2 * E + 2 * n * d * es  # CSR (upper bound) + both T buffers
+    cap = int(0.9 * whole_csr_t)
+    with pkg.Context(0) as ctx:
+        ctx.set_option("chunk_bytes", cap)
+        if out_on == "device":
+            out_t = torch.empty((n, d), dtype=torch.float32, device="cuda")
+            ids_t = torch.empty(n, dtype=torch.int64, device="cuda")
+            got_n = pkg.cleora_chunked_embed(ctx.handle, e.src, e.dst, None, None, False, d, iters, 4,
+                                             storage, ids_t, out_t)
+            torch.cuda.synchronize()
+            out, out_ids = out_t.cpu().numpy(), ids_t.cpu().numpy().view(np.uint64)
+        else:
+            if out_on == "pinned":
+                out = torch.empty((n, d), dtype=torch.float32, pin_memory=True).numpy()
+            else:
+                out = np.empty((n, d), np.float32)
+            out_ids = np.empty(n, np.uint64)
+            got_n = pkg.cleora_chunked_embed(ctx.handle, e.src, e.dst, None, None, False, d, iters, 4,
+                                             storage, out_ids, out)
+        info = pkg.cleora_chunked_info(ctx.handle)
+    Q = info["chunks"]
+    assert got_n == n and np.array_equal(out_ids, g_ids)
+    assert Q > 1 and whole_csr_t > cap
+    assert 0 < info["peak_device_bytes"] <= cap  # the device never held the whole graph
+    offs = [E * q // Q for q in range(Q + 1)]
+    if storage == "f32":
+        _, want = oracle.chunked_embed(e.src, e.dst, None, offs, False, d, iters, 4)
+        tol = 1e-5
+    else:  # every chunk starts from the BF16-rounded T_0
+        occ_all = np.zeros(n)
+        np.add.at(occ_all, np.searchsorted(g_ids, np.concatenate([e.src, e.dst])), 1.0)
+        want = np.zeros((n, d))
+        for q in range(Q):
+            s_, t_ = e.src[offs[q]:offs[q + 1]], e.dst[offs[q]:offs[q + 1]]
+            gq = oracle.build_graph(s_, t_, None, False)
+            Tq = oracle.propagate(gq, _bf16_round(oracle.init(gq.ids, d, 4)), iters)
+            occ = np.zeros(gq.n)
+            np.add.at(occ, np.searchsorted(gq.ids, np.concatenate([s_, t_])), 1.0)
+            v = np.searchsorted(g_ids, gq.ids)
+            want[v] += (occ / occ_all[v])[:, None] * Tq
+        tol = 2e-2
+    assert np.abs(out - want).max() <= tol
