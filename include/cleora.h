@@ -149,10 +149,9 @@ typedef enum {
                                     estimate of their number.  A set that fills up is
                                     rebuilt with 4 x num_edges slots, so any value gives the
                                     same graph                                             */
-    CLEORA_OPT_STAGING = 7,      /* how gathered rows reach the sums: 0 automatic (the ring
-                                    when the shape allows it and T is larger than twice the
-                                    hot-row budget), 1 = registers, 2 = a shared-memory ring
-                                    filled by bulk copies (rows of 32 x 8 or 32 x 16 bytes:
+    CLEORA_OPT_STAGING = 7,      /* how gathered rows reach the sums: 0 or 1 = registers
+                                    (the faster on GB300), 2 = a shared-memory ring filled by
+                                    one bulk copy per gathered row (rows of 32 x 8 or 32 x 16 bytes:
                                     FP32 d = 64 or 128, BF16 d = 128 or 256; other shapes use
                                     registers).  With the ring, rows keep ascending column
                                     order and hot entries are marked in a bitmap instead of
@@ -226,6 +225,43 @@ int cleora_chunked_embed(cleora_ctx* ctx, const uint64_t* src, const uint64_t* d
 /* Chunks of the last cleora_chunked_embed call and the high-water mark of the device memory
  * the library held during it (bytes, from the context's pool). */
 int cleora_chunked_info(const cleora_ctx* ctx, int* chunks, int64_t* peak_device_bytes);
+
+/* ---------------------------------------------------------------------------------------
+ * Identifiers and hypergraphs (Sec. 4.3: identifiers hashed with xxhash into a small
+ * fixed-width format; Sec. 3.2 "Hypergraph Expansion": clique and star expansion)
+ * ------------------------------------------------------------------------------------- */
+
+/* XXH64 (the xxHash specification, 64-bit variant, little-endian lanes) of every string
+ * bytes[offsets[i] .. offsets[i+1]), i < count, with `seed`, into out[count]: the uint64 ids the
+ * graph calls take.  offsets[0] must be 0.  bytes/offsets are host (inputs_on_device == 0) or
+ * device arrays, out host or device; the call returns when out is written.  Distinct strings
+ * can share a hash (about count^2 / 2^65 expected collisions), as in the paper's design. */
+int cleora_hash_ids(cleora_ctx* ctx, const uint8_t* bytes, const int64_t* offsets, int64_t count,
+                    uint64_t seed, uint64_t* out, int inputs_on_device, int out_on_device);
+
+typedef enum { CLEORA_EXPAND_CLIQUE = 0, CLEORA_EXPAND_STAR = 1 } cleora_expansion;
+
+/* Expands a hypergraph into undirected edges.  Hyperedge h (h < num_hyperedges) holds the ids
+ * members[hoff[h] .. hoff[h+1]) (hoff[0] = 0, non-decreasing); repeated members count once, so
+ * its distinct members in ascending id order u_0 < ... < u_{k-1} give
+ *   CLEORA_EXPAND_CLIQUE: the edges (u_i, u_j), i < j, in lexicographic (i, j) order --
+ *                         k(k-1)/2 edges (a hyperedge of one member gives none);
+ *   CLEORA_EXPAND_STAR:   the edges (s_h, u_i), i = 0..k-1 -- k edges, s_h the hyperedge's star
+ *                         node: star_ids[h], or when star_ids is NULL the splitmix64 output
+ *                         function of h ^ 0x5354415253544152 (ids the caller should keep
+ *                         apart from its members').
+ * Hyperedges keep their order.  *num_edges gets the edge count; src_out / dst_out (capacity
+ * edges each; NULL to only count) get the edges.  Inputs host or device (inputs_on_device),
+ * outputs host or device (out_on_device).  CLEORA_ERR_INVALID_ARG when the edges do not fit. */
+int cleora_expand_hypergraph(cleora_ctx* ctx, const uint64_t* members, const int64_t* hoff,
+                             int64_t num_hyperedges, int mode, const uint64_t* star_ids,
+                             int inputs_on_device, uint64_t* src_out, uint64_t* dst_out,
+                             int64_t capacity, int64_t* num_edges, int out_on_device);
+/* The same expansion kept on the device and built as the context's undirected graph, exactly
+ * as cleora_graph_build would build the expanded edge list (unit weights). */
+int cleora_hypergraph_build(cleora_ctx* ctx, const uint64_t* members, const int64_t* hoff,
+                            int64_t num_hyperedges, int mode, const uint64_t* star_ids,
+                            int inputs_on_device, int64_t* num_edges);
 
 /* ---------------------------------------------------------------------------------------
  * Batched small graphs: many independent graphs in one persistent launch per iteration

@@ -67,6 +67,11 @@ SIGNATURES = {
                                             ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_int, _P, _P, _I64, ctypes.POINTER(_I64),
                                             ctypes.c_int]),
+    "cleora_hash_ids": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_uint64, _P, ctypes.c_int, ctypes.c_int]),
+    "cleora_expand_hypergraph": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P, ctypes.c_int, _P, _P, _I64,
+                                                ctypes.POINTER(_I64), ctypes.c_int]),
+    "cleora_hypergraph_build": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P, ctypes.c_int,
+                                               ctypes.POINTER(_I64)]),
     "cleora_chunked_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)]),
     "cleora_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int]),
@@ -339,6 +344,67 @@ def cleora_chunked_info(ctx) -> dict:
     peak = _I64()
     _check(ctx, load().cleora_chunked_info(ctx, ctypes.byref(ctx_int), ctypes.byref(peak)))
     return {"chunks": q.value, "peak_device_bytes": peak.value}
+
+
+# ---- identifiers and hypergraphs ----------------------------------------------------------
+
+CLEORA_EXPAND_CLIQUE = 0
+CLEORA_EXPAND_STAR = 1
+EXPANSIONS = {"clique": CLEORA_EXPAND_CLIQUE, "star": CLEORA_EXPAND_STAR}
+
+
+def _same_place(*arrays):
+    devs = {_ptr(a)[1] for a in arrays if a is not None}
+    if len(devs) > 1:
+        raise ValueError("arrays must all be on the host or all on the device")
+    return devs.pop() if devs else 0
+
+
+def cleora_hash_ids(ctx, bytes_, offsets, seed=0, out=None):
+    """XXH64 of strings bytes_[offsets[i]:offsets[i+1]] (uint8 and int64 arrays) -> uint64 ids."""
+    count = int(offsets.shape[0]) - 1
+    if out is None:
+        out = np.empty(max(count, 0), np.uint64)
+    on_dev = _same_place(bytes_, offsets)
+    pb, _ = _ptr(bytes_)
+    po, _ = _ptr(offsets)
+    pout, dout = _ptr(out)
+    _check(ctx, load().cleora_hash_ids(ctx, pb, po, count, int(seed) & (2**64 - 1), pout, on_dev, dout))
+    return out
+
+
+def cleora_expand_hypergraph(ctx, members, hoff, mode="clique", star_ids=None, src_out=None, dst_out=None):
+    """Edges of the clique or star expansion; with no outputs given, host arrays sized by a
+    counting call are returned."""
+    H = int(hoff.shape[0]) - 1
+    on_dev = _same_place(members, hoff, star_ids)
+    m = EXPANSIONS[mode] if isinstance(mode, str) else int(mode)
+    pm, _ = _ptr(members)
+    ph, _ = _ptr(hoff)
+    ps, _ = _ptr(star_ids)
+    ne = _I64()
+    if src_out is None:
+        _check(ctx, load().cleora_expand_hypergraph(ctx, pm, ph, H, m, ps, on_dev, None, None, 0,
+                                                    ctypes.byref(ne), 0))
+        src_out = np.empty(ne.value, np.uint64)
+        dst_out = np.empty(ne.value, np.uint64)
+    psrc, dsrc = _ptr(src_out)
+    pdst, _ = _ptr(dst_out)
+    _check(ctx, load().cleora_expand_hypergraph(ctx, pm, ph, H, m, ps, on_dev, psrc, pdst,
+                                                int(src_out.shape[0]), ctypes.byref(ne), dsrc))
+    return src_out[:ne.value], dst_out[:ne.value]
+
+
+def cleora_hypergraph_build(ctx, members, hoff, mode="clique", star_ids=None) -> int:
+    H = int(hoff.shape[0]) - 1
+    on_dev = _same_place(members, hoff, star_ids)
+    m = EXPANSIONS[mode] if isinstance(mode, str) else int(mode)
+    pm, _ = _ptr(members)
+    ph, _ = _ptr(hoff)
+    ps, _ = _ptr(star_ids)
+    ne = _I64()
+    _check(ctx, load().cleora_hypergraph_build(ctx, pm, ph, H, m, ps, on_dev, ctypes.byref(ne)))
+    return ne.value
 
 
 # ---- batched small graphs -------------------------------------------------------------

@@ -222,6 +222,19 @@ __device__ __forceinline__ void fma2(float& a0, float& a1, float w, float x0, fl
     }
 }
 
+// a += one BF16 half of w (low or high), FP32 result: the mixed-precision add.f32.bf16 converts
+// the BF16 value exactly and rounds once, so it equals converting then adding.
+__device__ __forceinline__ float add_lo(float a, uint32_t w) {
+    float r;
+    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n add.rn.f32.bf16 %0, l, %2;}" : "=f"(r) : "r"(w), "f"(a));
+    return r;
+}
+__device__ __forceinline__ float add_hi(float a, uint32_t w) {
+    float r;
+    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n add.rn.f32.bf16 %0, h, %2;}" : "=f"(r) : "r"(w), "f"(a));
+    return r;
+}
+
 // Element traits: FP32 has one element per 32-bit word, BF16 two.
 template <typename ST> struct EL;
 template <> struct EL<float> {
@@ -253,10 +266,17 @@ constexpr int inflight() {
     return (VEC == 8 && CPL == 1 && G == 32) ? 4 : 8;
 }
 
-// INF: vectors in flight per lane (0: inflight()).
-template <typename ST, int VEC, int CPL, int G, bool HV, bool CHECK = false, int INF = 0>
+// INF: vectors in flight per lane (0: inflight()).  FR: full rows -- the row holds exactly
+// CPL x G vectors, so no lane's vector index needs a bound test and the row stride is a
+// compile-time constant.
+template <typename ST, int VEC, int CPL, int G, bool HV, bool CHECK = false, int INF = 0, bool FR = false>
 struct Kern {
     using VT = typename VecT<VEC>::T;
+    static constexpr int64_t FR_ROW = (int64_t)CPL * G * VEC;  // row bytes of full rows
+    __device__ static __forceinline__ bool in_row(const Args& a, int i, int lg) {
+        return FR || i * G + lg < a.chunks;
+    }
+    __device__ static __forceinline__ int64_t row_bytes(const Args& a) { return FR ? FR_ROW : a.row_bytes; }
     static constexpr int W = VEC / 4;                       // 32-bit words per vector
     static constexpr int EPV = W * EL<ST>::PER_WORD;        // elements per vector
     static constexpr int P = 32 / G;                        // lane groups per warp
@@ -287,6 +307,14 @@ struct Kern {
     };
 
     __device__ static __forceinline__ void add_vec(Acc& acc, int i, const VT& x, float w) {
+        if (!HV && std::is_same<ST, __nv_bfloat16>::value) {  // no unpacking: mixed adds
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                acc.v[i][2 * k] = add_lo(acc.v[i][2 * k], word(x, k));
+                acc.v[i][2 * k + 1] = add_hi(acc.v[i][2 * k + 1], word(x, k));
+            }
+            return;
+        }
         float f[EPV];
 #pragma unroll
         for (int k = 0; k < W; ++k) EL<ST>::unpack(word(x, k), f + k * EL<ST>::PER_WORD);
@@ -317,21 +345,21 @@ struct Kern {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u * P + g;
-            const int c = __shfl_sync(FULL, mc, j & 31);
-            const float wu = HV ? __shfl_sync(FULL, mw, j & 31) : 1.f;
+            const int c = __shfl_sync(FULL, mc, j);  // (the source lane is taken mod 32)
+            const float wu = HV ? __shfl_sync(FULL, mw, j) : 1.f;
             bool ok = FULLB || j < jh;
             if (CHECK && ok && (unsigned)c >= (unsigned)a.n) {  // corrupt index: flag, skip
                 atomicOr(a.err, 1);
                 ok = false;
             }
             w[u] = ok ? wu : 0.f;
-            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * a.row_bytes) + lg;
+            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * row_bytes(a)) + lg;
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 if (Tune<ST>::POLICY)
-                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G, cp) : zero_vec();
+                    x[u][i] = (ok && in_row(a, i, lg)) ? ld_gather(rp + i * G, cp) : zero_vec();
                 else
-                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G) : zero_vec();
+                    x[u][i] = (ok && in_row(a, i, lg)) ? ld_gather(rp + i * G) : zero_vec();
             }
         }
 #pragma unroll
@@ -350,21 +378,21 @@ struct Kern {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u;
-            const int c = __shfl_sync(gmask, mc, j & (G - 1), G);
-            const float wu = HV ? __shfl_sync(gmask, mw, j & (G - 1), G) : 1.f;
+            const int c = __shfl_sync(gmask, mc, j, G);  // (the source lane is taken mod G)
+            const float wu = HV ? __shfl_sync(gmask, mw, j, G) : 1.f;
             bool ok = FULLB || j < jh;
             if (CHECK && ok && (unsigned)c >= (unsigned)a.n) {
                 atomicOr(a.err, 1);
                 ok = false;
             }
             w[u] = ok ? wu : 0.f;
-            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * a.row_bytes) + lg;
+            const VT* rp = reinterpret_cast<const VT*>(a.Tin + (int64_t)c * row_bytes(a)) + lg;
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 if (Tune<ST>::POLICY)
-                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G, cp) : zero_vec();
+                    x[u][i] = (ok && in_row(a, i, lg)) ? ld_gather(rp + i * G, cp) : zero_vec();
                 else
-                    x[u][i] = (ok && i * G + lg < a.chunks) ? ld_gather(rp + i * G) : zero_vec();
+                    x[u][i] = (ok && in_row(a, i, lg)) ? ld_gather(rp + i * G) : zero_vec();
             }
         }
 #pragma unroll
@@ -389,11 +417,11 @@ struct Kern {
 
     // Own previous row (a row without entries keeps it, renormalised).
     __device__ static __forceinline__ void load_own(const Args& a, Acc& acc, int64_t r, int lg) {
-        const VT* rp = reinterpret_cast<const VT*>(a.Tin + r * a.row_bytes);
+        const VT* rp = reinterpret_cast<const VT*>(a.Tin + r * row_bytes(a));
 #pragma unroll
         for (int i = 0; i < CPL; ++i) {
             const int q = i * G + lg;
-            if (q < a.chunks) {
+            if (in_row(a, i, lg)) {
                 VT x = ld_gather(rp + q);
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
@@ -422,7 +450,7 @@ struct Kern {
         float ss = 0.f;
 #pragma unroll
         for (int i = 0; i < CPL; ++i) {
-            if (i * G + lg < a.chunks) {
+            if (in_row(a, i, lg)) {
 #pragma unroll
                 for (int e = 0; e < EPV; ++e) ss = fmaf(acc.t[i][e], acc.t[i][e], ss);
             }
@@ -431,11 +459,11 @@ struct Kern {
         for (int off = 1; off < G; off <<= 1) ss += __shfl_xor_sync(gmask, ss, off);
         const float inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
         if (!store) return;
-        VT* op = reinterpret_cast<VT*>(a.Tout + r * a.row_bytes);
+        VT* op = reinterpret_cast<VT*>(a.Tout + r * row_bytes(a));
 #pragma unroll
         for (int i = 0; i < CPL; ++i) {
             const int q = i * G + lg;
-            if (q < a.chunks) {
+            if (in_row(a, i, lg)) {
                 VT x;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
@@ -590,7 +618,7 @@ struct Kern {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 const int q = i * G + lg;
-                if (q < a.chunks) {
+                if (in_row(a, i, lg)) {
 #pragma unroll
                     for (int e = 0; e < EPV; ++e) __stcg(slot + q * EPV + e, acc.t[i][e]);
                 }
@@ -610,7 +638,7 @@ struct Kern {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 const int q = i * G + lg;
-                if (q < a.chunks) {
+                if (in_row(a, i, lg)) {
 #pragma unroll
                     for (int e = 0; e < EPV; ++e) acc.v[i][e] += __ldcg(s + q * EPV + e);
                 }
@@ -637,10 +665,10 @@ constexpr int min_blocks() {
     return 4;
 }
 
-template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
+template <typename ST, int VEC, int CPL, int G, int MODE, bool HV, bool FR = false>
 __global__ void __launch_bounds__(256, (min_blocks<ST, VEC, CPL, G, HV>()))
 k_propagate(Args a) {
-    using K = Kern<ST, VEC, CPL, G, HV>;
+    using K = Kern<ST, VEC, CPL, G, HV, false, 0, FR>;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
     for (;;) {
@@ -663,9 +691,9 @@ k_propagate(Args a) {
 // Host-side launcher for one storage type, vector width and value mode.
 template <typename ST, int VEC, bool HV>
 struct Launch {
-    template <int CPL, int G, int MODE>
+    template <int CPL, int G, int MODE, bool FR = false>
     static cudaError_t go(const Args& a, int blocks_per_sm, int num_sms, cudaStream_t s, int* grid_out) {
-        auto kern = k_propagate<ST, VEC, CPL, G, MODE, HV>;
+        auto kern = k_propagate<ST, VEC, CPL, G, MODE, HV, FR>;
         int bps = blocks_per_sm;
         if (bps <= 0) {
             cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0);
@@ -687,15 +715,17 @@ struct Launch {
                 case 4:  return m == 2 ? go<1, 4, 2>(a, bps, sms, s, grid) : go<1, 4, 1>(a, bps, sms, s, grid);
                 case 8:  return m == 2 ? go<1, 8, 2>(a, bps, sms, s, grid) : go<1, 8, 1>(a, bps, sms, s, grid);
                 case 16: return m == 2 ? go<1, 16, 2>(a, bps, sms, s, grid) : go<1, 16, 1>(a, bps, sms, s, grid);
-                case 32: return go<1, 32, 1>(a, bps, sms, s, grid);
+                case 32: return sh.chunks == 32 ? go<1, 32, 1, true>(a, bps, sms, s, grid)
+                                                : go<1, 32, 1>(a, bps, sms, s, grid);
                 default: return cudaErrorInvalidValue;
             }
         }
         if (sh.G != 32) return cudaErrorInvalidValue;
+        const bool full = sh.chunks == 32 * sh.cpl;
         switch (sh.cpl) {
-            case 2: return go<2, 32, 1>(a, bps, sms, s, grid);
-            case 4: return go<4, 32, 1>(a, bps, sms, s, grid);
-            case 8: return go<8, 32, 1>(a, bps, sms, s, grid);
+            case 2: return full ? go<2, 32, 1, true>(a, bps, sms, s, grid) : go<2, 32, 1>(a, bps, sms, s, grid);
+            case 4: return full ? go<4, 32, 1, true>(a, bps, sms, s, grid) : go<4, 32, 1>(a, bps, sms, s, grid);
+            case 8: return full ? go<8, 32, 1, true>(a, bps, sms, s, grid) : go<8, 32, 1>(a, bps, sms, s, grid);
             default: return cudaErrorInvalidValue;
         }
     }

@@ -105,18 +105,6 @@ template <int N>
 __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-// a += bf16 (low or high half of w), FP32 result, one rounding
-__device__ __forceinline__ float add_lo(float a, uint32_t w) {
-    float r;
-    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n add.rn.f32.bf16 %0, l, %2;}" : "=f"(r) : "r"(w), "f"(a));
-    return r;
-}
-__device__ __forceinline__ float add_hi(float a, uint32_t w) {
-    float r;
-    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n add.rn.f32.bf16 %0, h, %2;}" : "=f"(r) : "r"(w), "f"(a));
-    return r;
-}
-
 template <typename ST, int VEC, bool HV, int S>
 struct Ring {
     using L = Layout<ST, VEC, HV, S>;
@@ -255,8 +243,8 @@ struct Ring {
 #pragma unroll
                 for (int k = 0; k < K::W; ++k) {
                     const uint32_t w = prop::word(x, k);
-                    acc.v[0][2 * k] = add_lo(acc.v[0][2 * k], w);
-                    acc.v[0][2 * k + 1] = add_hi(acc.v[0][2 * k + 1], w);
+                    acc.v[0][2 * k] = prop::add_lo(acc.v[0][2 * k], w);
+                    acc.v[0][2 * k + 1] = prop::add_hi(acc.v[0][2 * k + 1], w);
                 }
             } else {
 #pragma unroll
