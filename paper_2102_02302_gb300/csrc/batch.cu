@@ -40,7 +40,7 @@ struct OneGraph {
 };
 
 struct Family {
-    int dtype = 0, vec = 16, cpl = 1;
+    int dtype = 0, vec = 16, cpl = 1, G = 32, mode = 1, hv = 0;
     BTask* tasks = nullptr;
     int64_t ntasks = 0;
     std::vector<int64_t> nt_step;  // nt_step[s]: tasks of graphs with iters >= s
@@ -154,10 +154,10 @@ int variant_for(const Shape& sh, bool hv) { return variant_of(sh.G, sh.mode, hv)
 
 cudaError_t launch_family(const Family& f, const BatchArgs& ba, int sms, cudaStream_t s) {
     if (f.dtype == CLEORA_F32)
-        return f.vec == 16 ? launch_batch_f32_v16(f.cpl, ba, sms, s, nullptr)
-                           : launch_batch_f32_v8(f.cpl, ba, sms, s, nullptr);
-    return f.vec == 16 ? launch_batch_bf16_v16(f.cpl, ba, sms, s, nullptr)
-                       : launch_batch_bf16_v8(f.cpl, ba, sms, s, nullptr);
+        return f.vec == 16 ? launch_batch_f32_v16(f.cpl, f.G, f.mode, ba, sms, s, nullptr)
+                           : launch_batch_f32_v8(f.cpl, f.G, f.mode, ba, sms, s, nullptr);
+    return f.vec == 16 ? launch_batch_bf16_v16(f.cpl, f.G, f.mode, ba, sms, s, nullptr)
+                       : launch_batch_bf16_v8(f.cpl, f.G, f.mode, ba, sms, s, nullptr);
 }
 
 }  // namespace batch
@@ -171,6 +171,9 @@ struct cleora_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches_per_run = 0;
+    std::vector<cudaStream_t> fstreams;  // one stream per kernel family
+    std::vector<cudaEvent_t> fevents;    // ... and its join event
+    cudaEvent_t fork = nullptr;
 };
 
 namespace cleora {
@@ -294,14 +297,15 @@ int pack(cleora_batch* b, const std::vector<int>& which, Packed& pk) {
     pk = Packed();
     pk.count = (int)order.size();
     pk.slot_of.assign(b->graphs.size(), -1);
-    std::map<std::tuple<int, int, int>, int> fam_index;
+    std::map<std::tuple<int, int, int, int, int, int>, int> fam_index;
     std::vector<int64_t> vecp(pk.count + 1, 0), outp(pk.count + 1, 0);
     int64_t split_off = 0, partial_off = 0;
     for (int k = 0; k < pk.count; ++k) {
         const OneGraph& og = b->graphs[order[k]];
         pk.slot_of[order[k]] = k;
         const int es = og.dtype == CLEORA_F32 ? 4 : 2;
-        auto key = std::make_tuple((int)og.dtype, og.shape.vec, og.shape.cpl);
+        auto key = std::make_tuple((int)og.dtype, og.shape.vec, og.shape.cpl, og.shape.G, og.shape.mode,
+                                   og.has_val ? 1 : 0);
         auto it = fam_index.find(key);
         int fam;
         if (it == fam_index.end()) {
@@ -311,6 +315,9 @@ int pack(cleora_batch* b, const std::vector<int>& which, Packed& pk) {
             f.dtype = og.dtype;
             f.vec = og.shape.vec;
             f.cpl = og.shape.cpl;
+            f.G = og.shape.G;
+            f.mode = og.shape.mode;
+            f.hv = og.has_val ? 1 : 0;
             pk.fams.push_back(f);
         } else {
             fam = it->second;
@@ -418,6 +425,26 @@ int enqueue(cleora_batch* b, Packed& pk, bool init, int s0, int s1, bool out, in
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return from_ctx(b, cuda_fail(c, e, "batch init", __FILE__, __LINE__));
     }
+    // Families are independent (disjoint graphs, own counters): each runs its steps on its own
+    // stream, forked from and joined back to the batch stream, so small families overlap.
+    if ((int)b->fstreams.size() < (int)pk.fams.size()) {
+        while ((int)b->fstreams.size() < (int)pk.fams.size()) {
+            cudaStream_t fs = nullptr;
+            cudaEvent_t ev = nullptr;
+            if ((e = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return from_ctx(b, cuda_fail(c, e, "family stream", __FILE__, __LINE__));
+            b->fstreams.push_back(fs);
+            b->fevents.push_back(ev);
+        }
+    }
+    if (b->fork == nullptr && (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
+        return from_ctx(b, cuda_fail(c, e, "fork event", __FILE__, __LINE__));
+    if ((e = cudaEventRecord(b->fork, s)) != cudaSuccess)
+        return from_ctx(b, cuda_fail(c, e, "fork", __FILE__, __LINE__));
+    for (size_t f = 0; f < pk.fams.size(); ++f)
+        if ((e = cudaStreamWaitEvent(b->fstreams[f], b->fork, 0)) != cudaSuccess)
+            return from_ctx(b, cuda_fail(c, e, "fork", __FILE__, __LINE__));
     for (int st = s0; st <= s1; ++st) {
         for (size_t f = 0; f < pk.fams.size(); ++f) {
             const Family& fam = pk.fams[f];
@@ -438,10 +465,16 @@ int enqueue(cleora_batch* b, Packed& pk, bool init, int s0, int s1, bool out, in
             ba.partials = pk.partials;
             ba.err = c->err_flag;
             ba.step = st;
+            ba.hv = fam.hv;
             ++nl;
-            if ((e = launch_family(fam, ba, sms, s)) != cudaSuccess)
+            if ((e = launch_family(fam, ba, sms, b->fstreams[f])) != cudaSuccess)
                 return from_ctx(b, cuda_fail(c, e, "batch step", __FILE__, __LINE__));
         }
+    }
+    for (size_t f = 0; f < pk.fams.size(); ++f) {  // join
+        if ((e = cudaEventRecord(b->fevents[f], b->fstreams[f])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, b->fevents[f], 0)) != cudaSuccess)
+            return from_ctx(b, cuda_fail(c, e, "join", __FILE__, __LINE__));
     }
     if (out && pk.total_out > 0) {
         k_batch_out<<<grid_for(pk.total_out / 4, 256, sms), 256, 0, s>>>(pk.gd, pk.count, pk.outv_prefix, pk.TA,
@@ -564,6 +597,9 @@ void cleora_batch_destroy(cleora_batch* b) {
         cudaStreamSynchronize(b->ctx->stream);
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
+        for (cudaStream_t fs : b->fstreams) cudaStreamDestroy(fs);
+        for (cudaEvent_t ev : b->fevents) cudaEventDestroy(ev);
+        if (b->fork) cudaEventDestroy(b->fork);
         for (OneGraph& og : b->graphs) free_graph_arrays(b->ctx, og);
         release_packed(b->ctx, b->pk);
         cleora_destroy(b->ctx);

@@ -4,8 +4,8 @@
 namespace cleora {
 namespace batch {
 
-cudaError_t launch_batch_bf16_v8(int cpl, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
-    return BatchLaunch<__nv_bfloat16, 8>::run(cpl, ba, sms, s, grid);
+cudaError_t launch_batch_bf16_v8(int cpl, int G, int mode, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+    return BatchLaunch<__nv_bfloat16, 8>::run(cpl, G, mode, ba, sms, s, grid);
 }
 
 }  // namespace batch

@@ -4,8 +4,8 @@
 namespace cleora {
 namespace batch {
 
-cudaError_t launch_batch_f32_v16(int cpl, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
-    return BatchLaunch<float, 16>::run(cpl, ba, sms, s, grid);
+cudaError_t launch_batch_f32_v16(int cpl, int G, int mode, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+    return BatchLaunch<float, 16>::run(cpl, G, mode, ba, sms, s, grid);
 }
 
 }  // namespace batch

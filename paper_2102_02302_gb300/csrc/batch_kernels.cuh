@@ -1,9 +1,9 @@
 // Batched propagation: many independent graphs packed into one multi-graph CSR and run by
 // one persistent launch per iteration step (per kernel family).
 //
-// A family is (storage type, gather bytes, vectors per lane); graphs whose d and storage
-// land in the same family share one launch, whatever their lane-group size, row mode or
-// value mode -- each task carries its graph, whose descriptor names the variant.  Every
+// A family is (storage type, gather bytes, vectors per lane, lanes per row); graphs whose d
+// and storage land in the same family share one launch, whatever their row mode or value
+// mode -- each task carries its graph, whose descriptor names the variant.  Every
 // task runs exactly the device code the single-graph kernel runs for that graph, on the
 // graph's own task plan, so a graph's result in the batch equals its single-graph result
 // bit for bit under the same schedule.
@@ -53,6 +53,7 @@ struct BatchArgs {
     float* partials;
     int* err;
     int step;  // 1-based; odd steps read TA and write TB
+    int hv;    // the family's graphs have per-entry values
 };
 
 constexpr int variant_of(int G, int mode, bool hv) {
@@ -61,49 +62,56 @@ constexpr int variant_of(int G, int mode, bool hv) {
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
 __device__ __forceinline__ void run_task(const prop::Args& a, const Task& t, int lane) {
-    // 4 vectors in flight for BF16 families (measured with the 4-CTA bound below)
-    using K = prop::Kern<ST, VEC, CPL, G, HV, false, std::is_same<ST, __nv_bfloat16>::value ? 4 : 0>;
+    // the single-graph kernel's vectors in flight for this shape (prop::inflight)
+    using K = prop::Kern<ST, VEC, CPL, G, HV>;
     const int g = lane / G, lg = lane % G;
     if (t.c >= 0) K::split_chunk(a, t, lane, g, lg);
     else if (MODE == 1 || G == 32) K::rows_coop(a, t.a, t.b, lane, g, lg);
     else K::rows_group(a, t.a, t.b, g, lg);
 }
 
-#define CLEORA_BV(G, MODE, HV) \
-    case variant_of(G, MODE, HV): run_task<ST, VEC, CPL, G, MODE, HV>(a, t, lane); break;
-
-template <typename ST, int VEC, int CPL>
-__device__ __forceinline__ void dispatch(int variant, const prop::Args& a, const Task& t, int lane) {
-    if constexpr (CPL == 1) {
-        switch (variant) {
-            CLEORA_BV(1, 1, false) CLEORA_BV(1, 2, false) CLEORA_BV(2, 1, false) CLEORA_BV(2, 2, false)
-            CLEORA_BV(4, 1, false) CLEORA_BV(4, 2, false) CLEORA_BV(8, 1, false) CLEORA_BV(8, 2, false)
-            CLEORA_BV(16, 1, false) CLEORA_BV(16, 2, false) CLEORA_BV(32, 1, false)
-            CLEORA_BV(1, 1, true) CLEORA_BV(1, 2, true) CLEORA_BV(2, 1, true) CLEORA_BV(2, 2, true)
-            CLEORA_BV(4, 1, true) CLEORA_BV(4, 2, true) CLEORA_BV(8, 1, true) CLEORA_BV(8, 2, true)
-            CLEORA_BV(16, 1, true) CLEORA_BV(16, 2, true) CLEORA_BV(32, 1, true)
-            default: if (lane == 0) atomicOr(a.err, 2); break;
-        }
-    } else {
-        switch (variant) {
-            CLEORA_BV(32, 1, false) CLEORA_BV(32, 1, true)
-            default: if (lane == 0) atomicOr(a.err, 2); break;
-        }
-    }
+__device__ __forceinline__ void fill_args(prop::Args& a, const BatchArgs& ba, const GDesc& gd, bool odd) {
+    a.rowptr = ba.rowptr + gd.node_off;
+    a.col = ba.col;
+    a.val = ba.val;
+    a.Tin = (odd ? ba.TA : ba.TB) + gd.T_off;
+    a.Tout = (odd ? ba.TB : ba.TA) + gd.T_off;
+    a.n = gd.n;
+    a.nnz = ba.total_nnz;
+    a.row_bytes = gd.row_bytes;
+    a.chunks = gd.chunks;
+    a.d = gd.d;
+    a.split_len = gd.split_len;
+    a.skip_len = INT64_MAX;
+    a.tasks = nullptr;
+    a.ntasks = 0;
+    a.counter = nullptr;
+    a.split_base = ba.split_base + gd.split_off;
+    a.split_count = ba.split_count + gd.split_off;
+    a.partials = ba.partials + gd.partial_off;
+    a.err = ba.err;
+    a.hot_cnt = nullptr;
+    a.hot_bits = nullptr;
+    a.test_wait_runout = 0;
 }
-#undef CLEORA_BV
 
-// BF16 families are compiled for 4 CTAs/SM (64 registers): the dispatch over every variant
-// of a family otherwise takes 94-110 registers, 2 CTAs/SM.  Measured on the 4096-graph batch:
-// 153 ms per replay unbounded, 125 ms at 3 CTAs, 113 ms at 4 (despite some spilling in the
-// 16-byte family).
-#ifndef CLEORA_BATCH_MINB
-#define CLEORA_BATCH_MINB 4
-#endif
-template <typename ST, int VEC, int CPL>
-__global__ void __launch_bounds__(256, (std::is_same<ST, __nv_bfloat16>::value && CPL <= 2) ? CLEORA_BATCH_MINB : 1)
+// A family is (storage, gather bytes, vectors per lane, lanes per row G, row mode, per-entry
+// values): its kernel runs exactly one variant of the single-graph kernel's device code.  A
+// task of another variant (none is ever packed into the family) raises bit 2 of the error
+// flag.
+// CTAs per SM a batch kernel is compiled for: a notch below its single-graph twin, whose
+// arguments sit in the parameter bank, while a batch task's arguments take registers.
+template <typename ST, int VEC, int CPL, int G, bool HV>
+constexpr int batch_min_blocks() {
+    constexpr int m = prop::min_blocks<ST, VEC, CPL, G, HV>();
+    return m >= 8 ? 6 : m >= 6 ? 5 : m >= 4 ? 3 : 1;
+}
+
+template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
+__global__ void __launch_bounds__(256, (batch_min_blocks<ST, VEC, CPL, G, HV>()))
 k_batch(BatchArgs ba) {
     const int lane = threadIdx.x & 31;
+    prop::Args a;
     const bool odd = ba.step & 1;
     for (;;) {
         unsigned long long t = 0;
@@ -112,35 +120,23 @@ k_batch(BatchArgs ba) {
         if (t >= (unsigned long long)ba.ntasks) break;
         const BTask bt = ba.tasks[t];
         const GDesc& gd = ba.gd[bt.g];
-        prop::Args a;
-        a.rowptr = ba.rowptr + gd.node_off;
-        a.col = ba.col;
-        a.val = ba.val;
-        a.Tin = (odd ? ba.TA : ba.TB) + gd.T_off;
-        a.Tout = (odd ? ba.TB : ba.TA) + gd.T_off;
-        a.n = gd.n;
-        a.nnz = ba.total_nnz;
-        a.row_bytes = gd.row_bytes;
-        a.chunks = gd.chunks;
-        a.d = gd.d;
-        a.split_len = gd.split_len;
-        a.tasks = nullptr;
-        a.ntasks = 0;
-        a.counter = nullptr;
-        a.split_base = ba.split_base + gd.split_off;
-        a.split_count = ba.split_count + gd.split_off;
-        a.partials = ba.partials + gd.partial_off;
-        a.err = ba.err;
-        dispatch<ST, VEC, CPL>(gd.variant, a, bt.t, lane);
+        fill_args(a, ba, gd, odd);
+        if (gd.variant == variant_of(G, MODE, HV)) run_task<ST, VEC, CPL, G, MODE, HV>(a, bt.t, lane);
+        else if (lane == 0) atomicOr(a.err, 2);
         __syncwarp();
     }
 }
 
+
 template <typename ST, int VEC>
 struct BatchLaunch {
-    template <int CPL>
+    template <int CPL, int G, int MODE = 1>
     static cudaError_t go(const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
-        auto kern = k_batch<ST, VEC, CPL>;
+        return ba.hv ? go_v<CPL, G, MODE, true>(ba, sms, s, grid) : go_v<CPL, G, MODE, false>(ba, sms, s, grid);
+    }
+    template <int CPL, int G, int MODE, bool HV>
+    static cudaError_t go_v(const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+        auto kern = k_batch<ST, VEC, CPL, G, MODE, HV>;
         int bps = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0);
         if (e != cudaSuccess) return e;
@@ -149,21 +145,33 @@ struct BatchLaunch {
         kern<<<bps * sms, 256, 0, s>>>(ba);
         return cudaGetLastError();
     }
-    static cudaError_t run(int cpl, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+    static cudaError_t run(int cpl, int G, int mode, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
+        const bool m2 = mode == 2;
+        if (cpl == 1) {
+            switch (G) {
+                case 1: return m2 ? go<1, 1, 2>(ba, sms, s, grid) : go<1, 1>(ba, sms, s, grid);
+                case 2: return m2 ? go<1, 2, 2>(ba, sms, s, grid) : go<1, 2>(ba, sms, s, grid);
+                case 4: return m2 ? go<1, 4, 2>(ba, sms, s, grid) : go<1, 4>(ba, sms, s, grid);
+                case 8: return m2 ? go<1, 8, 2>(ba, sms, s, grid) : go<1, 8>(ba, sms, s, grid);
+                case 16: return m2 ? go<1, 16, 2>(ba, sms, s, grid) : go<1, 16>(ba, sms, s, grid);
+                case 32: return go<1, 32>(ba, sms, s, grid);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+        if (G != 32) return cudaErrorInvalidValue;
         switch (cpl) {
-            case 1: return go<1>(ba, sms, s, grid);
-            case 2: return go<2>(ba, sms, s, grid);
-            case 4: return go<4>(ba, sms, s, grid);
-            case 8: return go<8>(ba, sms, s, grid);
+            case 2: return go<2, 32>(ba, sms, s, grid);
+            case 4: return go<4, 32>(ba, sms, s, grid);
+            case 8: return go<8, 32>(ba, sms, s, grid);
             default: return cudaErrorInvalidValue;
         }
     }
 };
 
-cudaError_t launch_batch_f32_v16(int cpl, const BatchArgs&, int sms, cudaStream_t, int*);
-cudaError_t launch_batch_f32_v8(int cpl, const BatchArgs&, int sms, cudaStream_t, int*);
-cudaError_t launch_batch_bf16_v16(int cpl, const BatchArgs&, int sms, cudaStream_t, int*);
-cudaError_t launch_batch_bf16_v8(int cpl, const BatchArgs&, int sms, cudaStream_t, int*);
+cudaError_t launch_batch_f32_v16(int cpl, int G, int mode, const BatchArgs&, int sms, cudaStream_t, int*);
+cudaError_t launch_batch_f32_v8(int cpl, int G, int mode, const BatchArgs&, int sms, cudaStream_t, int*);
+cudaError_t launch_batch_bf16_v16(int cpl, int G, int mode, const BatchArgs&, int sms, cudaStream_t, int*);
+cudaError_t launch_batch_bf16_v8(int cpl, int G, int mode, const BatchArgs&, int sms, cudaStream_t, int*);
 
 }  // namespace batch
 }  // namespace cleora

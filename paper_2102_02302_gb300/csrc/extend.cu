@@ -357,12 +357,14 @@ int cleora_chunked_embed(cleora_ctx* ctx, const uint64_t* src, const uint64_t* d
         unsigned long long zero = 0;
         cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &zero);
     }
+    // a chunk's peak: the serving estimate of its build and embedding, taken for FP32 storage
+    // (BF16 needs no more; the estimate's BF16 term is for result staging, which chunks skip)
     auto chunk_estimate = [&](int64_t Eq) -> int64_t {
         cleora_job j{};
         j.num_edges = Eq;
         j.directed = directed;
         j.d = d;
-        j.storage = storage;
+        j.storage = CLEORA_F32;
         j.weights = weights;
         return cleora_serve_estimate(&j);
     };

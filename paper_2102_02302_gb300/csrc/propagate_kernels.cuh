@@ -263,7 +263,10 @@ template <> struct EL<__nv_bfloat16> {
 template <typename ST, int VEC, int CPL, int G>
 constexpr int inflight() {
     if (Tune<ST>::INFLIGHT > 0) return Tune<ST>::INFLIGHT;
-    return (VEC == 8 && CPL == 1 && G == 32) ? 4 : 8;
+    if (VEC == 8 && CPL == 1 && G == 32) return 4;
+    // lane groups of 16-byte gathers: 8 in flight do not fit the 64 registers of 4 CTAs/SM
+    if (VEC == 16 && G < 32) return 4;
+    return 8;
 }
 
 // INF: vectors in flight per lane (0: inflight()).  FR: full rows -- the row holds exactly
