@@ -493,7 +493,7 @@ def batch_measure(device, steps, warmup, count=4096, peak=None, peak_kind="measu
 # Serving: Poisson arrivals at 80% of measured capacity, p50/p99 arrival -> result on host
 # ---------------------------------------------------------------------------------------
 
-def serve_pool(count=24, seed=0):
+def serve_pool(count=48, seed=0):
     """Job graphs: n log-uniform in [1e3, 5e6] (quantiles), average degree U[5, 40],
     undirected unit-weight Chung-Lu (exponent 2.1), generated on the GPU, kept in pinned
     host memory."""
@@ -636,18 +636,32 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
     work = sum(r.nnz * j[1] * j[2] for r, j in zip(results[warm:], jobs[warm:]))
     big = np.array([pool[j[0]]["n"] * j[1] for j in jobs])[warm:]
     q = np.percentile(big, 90)
+    # latency per size class: quartiles of the job's work (pool graph edges * d * I)
+    work_j = np.array([pool[j[0]]["edges"] * j[1] * j[2] for j in jobs])[warm:]
+    edges_q = np.percentile(work_j, [25, 50, 75])
+    cls = np.searchsorted(edges_q, work_j, side="right")
+    by_size = []
+    for c in range(4):
+        sel = lat[cls == c]
+        if sel.size:
+            by_size.append({"class": f"work quartile {c + 1}", "jobs": int(sel.size),
+                            "p50_ms": float(np.percentile(sel, 50) * 1e3),
+                            "p99_ms": float(np.percentile(sel, 99) * 1e3)})
     return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "failed": n_jobs - len(ok),
             "capacity_jobs_per_s": capacity, "lambda_jobs_per_s": lam,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "queue_wait_p50_ms": float(np.percentile(wait, 50) * 1e3),
             "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
             "service_p99_ms": float(np.percentile(svc, 99) * 1e3),
+            "by_size": by_size,
+            "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
+            "admission": "earliest virtual finish (arrival + estimated service) among jobs that fit the budget",
             "p99_ms_largest_10pct": float(np.percentile(lat[big >= q], 99) * 1e3),
             "p99_ms_other_90pct": float(np.percentile(lat[big < q], 99) * 1e3),
             "jobs_per_s": (n_jobs - warm) / span, "nnz_d_iters_per_s": work / span,
             "pool_graphs": len(pool), "setup_s": gen_s, "output_arena_gb": arena_bytes / 2**30,
             "latency_def": "Poisson arrival time to FP32 result in (pinned) host memory",
-            "job_mix": "n log-uniform [1e3, 5e6] (24-graph pool, nearest n), degree U[5, 40], "
+            "job_mix": "n log-uniform [1e3, 5e6] (48-graph pool, nearest n), degree U[5, 40], "
                        "d in {64,128,256,1024}, I in {3,4,5}, FP32/BF16 50/50"}
 
 

@@ -358,9 +358,12 @@ typedef struct {
 
 /* Starts the server: max_slots worker threads, each with its own context and stream, on
  * `device`.  Admission: a waiting job starts when a slot is free and its estimated peak
- * device bytes (cleora_serve_estimate) fit in the budget next to the running jobs; jobs are
- * scanned in arrival order and a later job may start ahead of one that does not fit, unless
- * that one has been passed over 8 times.  Jobs on different slots overlap on the GPU.  After
+ * device bytes (cleora_serve_estimate) fit in the budget next to the running jobs.  Among
+ * the jobs that fit, the one with the earliest virtual finish time starts first: arrival time
+ * plus an estimated service time (a cost model of its host transfers, graph build and
+ * gathered bytes), so short jobs go ahead of long ones while a job is only passed by jobs
+ * that arrived within its own service estimate after it.  A job passed over 8 times because
+ * it did not fit stops later jobs from passing it.  Jobs on different slots overlap on the GPU.  After
  * a job, its slot returns the memory it held to the driver (pool trim) except a cache of
  * min(1 GiB, budget / (8 slots)) per slot, which is set aside from the budget, so the budget
  * tracks what running jobs and the slot caches hold. */

@@ -1,10 +1,12 @@
 // Serving runtime (include/cleora.h, cleora_serve_*): a continuous-batching request loop.
 //
 // Slots.  max_slots worker threads, each owning a context (stream + memory pool).  A worker
-// that is free takes the first waiting job that fits: a slot is free and the job's
-// estimated peak device bytes fit in the budget beside the running jobs' reservations.
-// Jobs are scanned in arrival order; a job passed over 8 times blocks further passing, so
-// a large job is not starved.  A job runs the whole method on its slot's stream (upload
+// that is free takes the waiting job with the earliest virtual finish time -- its arrival
+// plus its estimated service time (a cost model of its host transfers, graph build and
+// gathered bytes) -- among those whose estimated peak device bytes fit in the budget beside
+// the running jobs' reservations.  Short jobs thus go ahead of long ones, but a job is only
+// passed by jobs that arrived less than its own service estimate after it, so every job
+// progresses; and a job passed over 8 times for lack of memory blocks further passing.  A job runs the whole method on its slot's stream (upload
 // and build, init, iterations, FP32 result to host), so jobs on different slots overlap on
 // the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver down
 // to a small per-slot cache (charged to the budget up front), and returns the reservation;
@@ -34,13 +36,26 @@ enum JobState { WAITING, RUNNING, DONE };
 struct Job {
     uint64_t id = 0;
     cleora_job spec;
-    int64_t est = 0;
+    int64_t est = 0;       // estimated peak device bytes
+    double key = 0.0;      // arrival + estimated service seconds: admission order
     int bypassed = 0;
     JobState state = WAITING;
     cleora_result res;
 };
 
 constexpr int MAX_BYPASS = 8;
+
+// Estimated service seconds of a job on a GB300 (only the order of jobs depends on it): a
+// fixed cost per job, edges up and FP32 rows down over the host link (~50 GB/s), the graph
+// build (~3e9 edges/s) and I iterations of gathered rows (~3e12 bytes/s).
+double service_estimate(const cleora_job& j) {
+    const double E = (double)j.num_edges;
+    const double m = j.directed ? E : 2.0 * E;
+    const double n = j.nodes_hint > 0 ? (double)j.nodes_hint : std::min(2.0 * E, 2147483647.0);
+    const double es = j.storage == CLEORA_F32 ? 4.0 : 2.0;
+    return 5e-3 + (E * (16.0 + (j.weights ? 4.0 : 0.0)) + n * j.d * 4.0) / 50e9 + E / 3e9 +
+           j.iters * m * j.d * es / 3e12;
+}
 
 }  // namespace serve
 }  // namespace cleora
@@ -104,7 +119,12 @@ void worker_main(cleora_server* s, int slot) {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
                 if (s->stop) return;
-                // first fit in arrival order, unless the head has been passed over too often
+                // earliest virtual finish that fits; a job passed over too often for lack of
+                // memory stops the scan (its turn comes when memory is returned)
+                std::stable_sort(s->queue.begin(), s->queue.end(),
+                                 [](const std::shared_ptr<Job>& x, const std::shared_ptr<Job>& y) {
+                                     return x->key < y->key;
+                                 });
                 for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
                     if (s->reserved + (*it)->est <= s->budget) {
                         job = *it;
@@ -114,8 +134,8 @@ void worker_main(cleora_server* s, int slot) {
                     if ((*it)->bypassed >= MAX_BYPASS) break;
                 }
                 if (job) {
-                    for (auto& q : s->queue)  // everyone ahead of it was passed over
-                        if (q->id < job->id) q->bypassed++;
+                    for (auto& q : s->queue)  // every job ahead of it did not fit
+                        if (q->key < job->key) q->bypassed++;
                     break;
                 }
                 s->cv_work.wait(lk);
@@ -246,6 +266,7 @@ int cleora_serve_submit(cleora_server* s, const cleora_job* job, uint64_t* job_i
             return CLEORA_ERR_REJECTED;
         j->id = s->next_id++;
         j->res.t_submit = s->now();
+        j->key = j->res.t_submit + service_estimate(*job);
         s->queue.push_back(j);
         s->jobs[j->id] = j;
         *job_id = j->id;

@@ -68,14 +68,20 @@ def test_results_alone_equal_results_in_the_mix(jobs):
         assert r.n == a.shape[0]
         assert r.t_submit <= r.t_admit <= r.t_done
         assert np.array_equal(o, a)
-    # and the mix still matches the oracle
-    for j, o in list(zip(jobs, outs))[:3]:
+    # and every job of the mix matches the oracle (BF16 jobs from the BF16-rounded T_0)
+    for j, o in zip(jobs, outs):
         g = oracle.build_from(j["edges"])
         T0 = oracle.init(g.ids, j["d"], j["seed"])
         if j["storage"] == "bf16":
-            continue
-        want = oracle.propagate(g, T0, j["iters"])
-        assert np.abs(o.astype(np.float64) - want).max() <= 1e-5
+            b = T0.astype(np.float32).view(np.uint32).astype(np.uint64)
+            T0 = ((((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint32) << 16).view(np.float32)
+            want = oracle.propagate(g, T0.astype(np.float64), j["iters"])
+            assert np.abs(o.astype(np.float64) - want).max() <= 2e-2
+            cos = (o * want).sum(1) / (np.linalg.norm(o, axis=1) * np.linalg.norm(want, axis=1))
+            assert cos.min() >= 0.999
+        else:
+            want = oracle.propagate(g, T0, j["iters"])
+            assert np.abs(o.astype(np.float64) - want).max() <= 1e-5
     # work overlapped on the device: some jobs ran at the same time
     spans = sorted((r.t_admit, r.t_done) for r in results)
     assert any(spans[k + 1][0] < spans[k][1] for k in range(len(spans) - 1))
@@ -109,16 +115,23 @@ def test_cancel_timeout_injected_failure_and_bad_input(jobs):
     # one slot and a slow first job keep the later jobs waiting long enough to cancel one
     blocker = dict(edges=synth.chung_lu_undirected(200_000, 2_000_000, 2.1, 7, 50_000.0), d=1024,
                    iters=5, seed=1, storage="f32")
+    import time
     with pkg.Server(0, max_slots=1, inject_alloc_failure_every=2) as srv:
-        ids = [_submit(srv, j, None) for j in [blocker] + jobs[:5]]
+        ids = [_submit(srv, blocker, None)]
+        t_end = time.time() + 60
+        while srv.stats()["running"] == 0 and time.time() < t_end:  # the blocker holds the slot
+            time.sleep(0.001)
+        ids += [_submit(srv, j, None) for j in jobs[:5]]
         # poll with a zero timeout on a job that cannot be done yet
         assert srv.poll(ids[-1], 0) is None
         assert srv.cancel(ids[-1]) == 0
         res = [srv.poll(i, 60_000) for i in ids]
         assert res[-1].status == pkg.CLEORA_ERR_CANCELLED
-        statuses = [r.status for r in res[:-1]]
-        # admitted jobs 2 and 4 had their first device allocation fail (host-side hook)
-        assert statuses == [0, pkg.CLEORA_ERR_OOM, 0, pkg.CLEORA_ERR_OOM, 0]
+        # in admission order, the 2nd and 4th admitted jobs had their first device allocation
+        # fail (host-side hook); admission follows the jobs' estimated virtual finish times
+        ran = sorted(res[:-1], key=lambda r: r.t_admit)
+        assert [r.status for r in ran] == [0, pkg.CLEORA_ERR_OOM, 0, pkg.CLEORA_ERR_OOM, 0]
+        assert ran[0].t_done <= ran[1].t_admit  # one slot: the blocker ran first
         # the server keeps serving after failures
         jid = _submit(srv, jobs[0], None)
         assert srv.poll(jid, 60_000).status in (0, pkg.CLEORA_ERR_OOM)
@@ -130,6 +143,28 @@ def test_cancel_timeout_injected_failure_and_bad_input(jobs):
         jid = srv.submit(e.src, e.dst, w, False, 16, 3)
         r = srv.poll(jid, 60_000)
         assert r.status in (pkg.CLEORA_ERR_INVALID_ARG, pkg.CLEORA_ERR_OOM)
+
+
+def test_short_jobs_pass_a_long_one_that_arrived_just_before():
+    import time
+    import paper_2102_02302_gb300 as pkg
+    # one slot: a blocker runs; then a long job and, right after it, short ones are queued.
+    # The short ones' virtual finish times (arrival + estimated service) come first.
+    blocker = synth.chung_lu_undirected(200_000, 2_000_000, 2.1, 7, 50_000.0)
+    long_job = synth.chung_lu_undirected(400_000, 4_000_000, 2.1, 8, 80_000.0)
+    short = [synth.chung_lu_undirected(300, 900, 2.1, k, 40.0) for k in range(4)]
+    with pkg.Server(0, max_slots=1) as srv:
+        b = srv.submit(blocker.src, blocker.dst, None, False, 256, 4)
+        t_end = time.time() + 60
+        while srv.stats()["running"] == 0 and time.time() < t_end:
+            time.sleep(0.001)
+        lj = srv.submit(long_job.src, long_job.dst, None, False, 256, 4)
+        sj = [srv.submit(e.src, e.dst, None, False, 16, 3) for e in short]
+        res_long = srv.poll(lj, 120_000)
+        res_short = [srv.poll(i, 120_000) for i in sj]
+        srv.poll(b, 120_000)
+    assert res_long.status == 0 and all(r.status == 0 for r in res_short)
+    assert all(r.t_done <= res_long.t_admit for r in res_short)
 
 
 def test_next_returns_every_job_once_in_completion_order(jobs):
