@@ -428,7 +428,7 @@ def generate_batch(count=4096, seed=0, workers=None):
     return specs, edges
 
 
-def batch_measure(device, steps, warmup, count=4096, peak=None, peak_kind="measured"):
+def batch_measure(device, steps, warmup, count=4096, peak=None, peak_kind="measured", autotune=True):
     import torch
     import paper_2102_02302_gb300 as pkg
     t = time.perf_counter()
@@ -438,7 +438,7 @@ def batch_measure(device, steps, warmup, count=4096, peak=None, peak_kind="measu
               "iters": sp.iters, "seed": sp.seed, "storage": "bf16"} for sp, e in zip(specs, edges)]
     stream = torch.cuda.Stream(device)
     t = time.perf_counter()
-    with pkg.Batch(descs, device, stream.cuda_stream, autotune=True) as b:
+    with pkg.Batch(descs, device, stream.cuda_stream, autotune=autotune) as b:
         create_s = time.perf_counter() - t
         del descs, edges
         tot = b.totals
@@ -483,6 +483,7 @@ def batch_measure(device, steps, warmup, count=4096, peak=None, peak_kind="measu
             "kernel_sha": source_sha(BATCH_SOURCES)}
     return {"graphs": count, "storage": "bf16", "nodes": tot["nodes"], "nnz": tot["nnz"],
             "roofline": roof,
+            "autotune": autotune,
             "nnz_d_iters": work, "value": work / (run_ms * 1e-3), "unit": "nnz*d/s",
             "run_ms": run_ms, "launches_per_run": launches, "max_iters": tot["max_iters"],
             "schedules": sched, "generate_s": gen_s, "create_s": create_s,
@@ -776,6 +777,7 @@ def main():
                     help="skip the 10k-node and 2M-node workloads (GPU and full oracle runs)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-autotune", type=int, default=1, help="1: autotuned schedules, 0: defaults")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -796,7 +798,8 @@ def main():
         import torch
         rank, local_rank, world = env_rank()
         torch.cuda.set_device(local_rank)
-        r = batch_measure(local_rank, args.steps, args.warmup, args.batch_count)
+        r = batch_measure(local_rank, args.steps, args.warmup, args.batch_count,
+                          autotune=bool(args.batch_autotune))
         if rank == 0:
             print(json.dumps({"metric": "nnz*d/s per iteration", "value": r["value"],
                               "unit": "nnz*d/s", "n_gpus": world, "steps": args.steps,
@@ -904,7 +907,8 @@ def main():
 
     batched = None
     if not args.no_batch:
-        batched = batch_measure(device, args.steps, args.warmup, args.batch_count, peak, peak_kind)
+        batched = batch_measure(device, args.steps, args.warmup, args.batch_count, peak, peak_kind,
+                                autotune=bool(args.batch_autotune))
         batched["value"] *= world
 
     serving = None

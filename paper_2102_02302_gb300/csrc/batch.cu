@@ -518,15 +518,15 @@ int autotune(cleora_batch* b) {
         std::vector<int>& members = kv.second;
         std::vector<Shape> cands = candidates(d, (cleora_dtype)dt);
         if (cands.size() < 2) continue;
-        // sample: up to 32 graphs spread over the class's sizes, at most ~8M entries
+        // sample: up to 64 graphs spread over the class's sizes, at most ~16M entries
         std::vector<int> byn(members);
         std::sort(byn.begin(), byn.end(), [&](int x, int y) { return b->graphs[x].nnz < b->graphs[y].nnz; });
         std::vector<int> sample;
-        const int want = std::min<int>(32, (int)byn.size());
+        const int want = std::min<int>(64, (int)byn.size());
         int64_t nnz_sum = 0;
         for (int k = 0; k < want; ++k) {
             const int idx = byn[(size_t)k * byn.size() / want];
-            if (nnz_sum > 8000000 && !sample.empty()) break;
+            if (nnz_sum > 16000000 && !sample.empty()) break;
             sample.push_back(idx);
             nnz_sum += b->graphs[idx].nnz;
         }
@@ -538,7 +538,7 @@ int autotune(cleora_batch* b) {
             if ((rc = pack(b, sample, mini)) != CLEORA_OK) break;
             float ms = 0.f;
             rc = enqueue(b, mini, true, 1, 1, false, nullptr);  // warm-up
-            for (int rep = 0; rep < 3 && rc == CLEORA_OK; ++rep) {
+            for (int rep = 0; rep < 5 && rc == CLEORA_OK; ++rep) {
                 cudaEventRecord(e0, c->stream);
                 rc = enqueue(b, mini, false, 1, 1, false, nullptr);
                 cudaEventRecord(e1, c->stream);
