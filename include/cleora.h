@@ -149,9 +149,11 @@ typedef enum {
                                     estimate of their number.  A set that fills up is
                                     rebuilt with 4 x num_edges slots, so any value gives the
                                     same graph                                             */
-    CLEORA_OPT_STAGING = 7,      /* how gathered rows reach the sums: 0 or 1 = registers
-                                    (the faster on GB300), 2 = a shared-memory ring filled by
-                                    one bulk copy per gathered row (rows of 32 x 8 or 32 x 16 bytes:
+    CLEORA_OPT_STAGING = 7,      /* how gathered rows reach the sums: 0 or 1 = registers,
+                                    2 = a shared-memory ring filled by one bulk copy per
+                                    gathered row, 3 = the same ring filled by TMA tensor
+                                    gathers of 4 rows (set before cleora_init, which builds the
+                                    tensor maps) (rows of 32 x 8 or 32 x 16 bytes:
                                     FP32 d = 64 or 128, BF16 d = 128 or 256; other shapes use
                                     registers).  With the ring, rows keep ascending column
                                     order and hot entries are marked in a bitmap instead of

@@ -407,6 +407,7 @@ int cleora_init(cleora_ctx* ctx, int d, uint64_t seed, cleora_dtype storage) {
     int rc = plan_ensure(ctx);
     if (rc == CLEORA_OK) rc = init_impl(ctx, seed);
     if (rc == CLEORA_OK) rc = hot_partition(ctx);
+    if (rc == CLEORA_OK) rc = ring_tensor_maps(ctx);
     if (rc != CLEORA_OK) { embeddings_release(ctx); return rc; }
     ctx->cur = 0;
     ctx->iteration = 0;
@@ -482,7 +483,7 @@ int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value) {
             if (value < 0) return fail(ctx, CLEORA_ERR_INVALID_ARG, "id slots");
             break;
         case CLEORA_OPT_STAGING:
-            if (value < 0 || value > 2) return fail(ctx, CLEORA_ERR_INVALID_ARG, "staging");
+            if (value < 0 || value > 3) return fail(ctx, CLEORA_ERR_INVALID_ARG, "staging");
             break;
         case CLEORA_OPT_RING_STAGES:
             if (value != 0 && (value < 2 || value > 4)) return fail(ctx, CLEORA_ERR_INVALID_ARG, "ring stages");

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -91,6 +92,8 @@ struct cleora_ctx {
     int iteration = 0;
 
     int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    CUtensorMap tmap[2];            // ring with 4-row tensor gathers: maps over T[0], T[1]
+    bool tmap_ready = false;
     int chunks_used = 0;            // cleora_chunked_embed: chunks of the last call
     int64_t chunk_peak_bytes = 0;   // ... and the pool's high-water mark during it
     int* err_flag = nullptr;  // device int, raised by kernels
@@ -209,6 +212,7 @@ int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout);
 // 32 x 8 or 32 x 16 bytes.
 inline bool ring_shape(const Shape& sh) { return sh.G == 32 && sh.cpl == 1 && sh.chunks == 32; }
 bool use_ring(const cleora_ctx* ctx);          // the current (d, storage, options) runs the ring
+int ring_tensor_maps(cleora_ctx* ctx);         // tensor maps over T for the 4-row gathers (init)
 constexpr int DEFAULT_RING_STAGES = 3;
 int hot_partition(cleora_ctx* ctx);            // partition rows hot-first (after init)
 int hot_restore(cleora_ctx* ctx);              // back to ascending column order

@@ -8,8 +8,10 @@
 // chunks, then the runs in row order.  The plan is built on the device and depends only on
 // the graph and the two sizes, never on timing, so the summation order of every row is
 // fixed by the graph's shape.
+#include <mutex>
 #include <vector>
 
+#include <cudaTypedefs.h>
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_sort.cuh>
 #include <cub/device/device_select.cuh>
@@ -453,7 +455,40 @@ int hot_restore(cleora_ctx* ctx) {
 bool use_ring(const cleora_ctx* ctx) {
     if (ctx->d == 0) return false;
     const Shape sh = choose_shape(ctx, ctx->d, ctx->dtype);
-    return ring_shape(sh) && ctx->opt[CLEORA_OPT_STAGING] == 2;
+    return ring_shape(sh) && (ctx->opt[CLEORA_OPT_STAGING] == 2 || ctx->opt[CLEORA_OPT_STAGING] == 3);
+}
+
+// Tensor maps over both embedding buffers for the ring's 4-row gathers: a 2-D tensor of n rows
+// of d elements (row stride d * element bytes), box d x 1 (one row per gathered coordinate).
+int ring_tensor_maps(cleora_ctx* ctx) {
+    ctx->tmap_ready = false;
+    if (!use_ring(ctx) || ctx->opt[CLEORA_OPT_STAGING] != 3 || ctx->g.n == 0) return CLEORA_OK;
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    });
+    if (!encode) return fail(ctx, CLEORA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const int es = ctx->dtype == CLEORA_F32 ? 4 : 2;
+    const cuuint64_t dims[2] = {(cuuint64_t)ctx->d, (cuuint64_t)ctx->g.n};
+    const cuuint64_t strides[1] = {(cuuint64_t)ctx->d * es};
+    const cuuint32_t box[2] = {(cuuint32_t)ctx->d, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult r = encode(&ctx->tmap[k],
+                                  ctx->dtype == CLEORA_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                  2, ctx->T[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(ctx, CLEORA_ERR_CUDA, "tensor map encoding failed (%d)", (int)r);
+    }
+    ctx->tmap_ready = true;
+    return CLEORA_OK;
 }
 
 // Marks the entries that point at the rows with the largest in-degree, as many rows as fit
@@ -664,12 +699,19 @@ int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
         a.hot_bits = g.hot_bits;
         a.test_wait_runout = (int)ctx->opt[CLEORA_OPT_TEST_RING_WAIT];
         const int st = ctx->opt[CLEORA_OPT_RING_STAGES] ? (int)ctx->opt[CLEORA_OPT_RING_STAGES] : DEFAULT_RING_STAGES;
+        const CUtensorMap* tm = nullptr;
+        if (ctx->opt[CLEORA_OPT_STAGING] == 3) {
+            if (!ctx->tmap_ready) return fail(ctx, CLEORA_ERR_STATE, "no tensor maps: init again after setting staging");
+            const int k = Tin == ctx->T[0] ? 0 : (Tin == ctx->T[1] ? 1 : -1);
+            if (k < 0) return fail(ctx, CLEORA_ERR_STATE, "ring gathers read the context's embeddings only");
+            tm = &ctx->tmap[k];
+        }
         if (ctx->dtype == CLEORA_F32)
-            e = sh.vec == 16 ? ring::launch_f32_v16(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid)
-                             : ring::launch_f32_v8(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid);
+            e = sh.vec == 16 ? ring::launch_f32_v16(a, tm, g.has_val, st, ctx->num_sms, ctx->stream, &grid)
+                             : ring::launch_f32_v8(a, tm, g.has_val, st, ctx->num_sms, ctx->stream, &grid);
         else
-            e = sh.vec == 16 ? ring::launch_bf16_v16(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid)
-                             : ring::launch_bf16_v8(a, g.has_val, st, ctx->num_sms, ctx->stream, &grid);
+            e = sh.vec == 16 ? ring::launch_bf16_v16(a, tm, g.has_val, st, ctx->num_sms, ctx->stream, &grid)
+                             : ring::launch_bf16_v8(a, tm, g.has_val, st, ctx->num_sms, ctx->stream, &grid);
         ctx->launches++;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "propagate launch", __FILE__, __LINE__);
         return CLEORA_OK;

@@ -22,11 +22,19 @@
 //    of every row) in FP32; BF16 values are added with the mixed-precision add.f32.bf16
 //    (exact conversion, one rounding: the same result as converting then adding).  Row ends
 //    inside a window close the row: norm by a shuffle butterfly, one streaming store.
+//  * G4 (option staging = 3): instead of one bulk copy per row, lanes 0..7 each issue one TMA
+//    tensor gather of 4 rows (cp.async.bulk.tensor.2d ... tile::gather4, a tensor map over T
+//    with a one-row box) into 4 consecutive slots: 8 requests per window instead of 32.  The
+//    L2 policy of a gather follows the majority of its 4 entries' hot bits.
 //  * Every mbarrier wait is bounded; a wait that runs out raises bit 4 of the error flag,
 //    the warp waits (bounded) for its copies in flight and leaves.
 // Summation order is fixed by the graph and the task plan (windows of 32 entries from the
 // task start, two-level sums), so results are deterministic.
 #pragma once
+
+#include <cuda.h>
+
+#include <cstring>
 
 #include "propagate_kernels.cuh"
 
@@ -97,6 +105,15 @@ __device__ __forceinline__ void bulk_row(uint32_t dst, const void* src, uint32_t
         "l"(src), "r"(bytes), "r"(bar), "l"(pol)
         : "memory");
 }
+// Four rows r0..r3 of the tensor map's 2-D tensor (box: one row) into dst, dst + ROW, ...
+__device__ __forceinline__ void gather4_rows(uint32_t dst, const CUtensorMap* tm, int32_t r0, int32_t r1, int32_t r2,
+                                             int32_t r3, uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(dst),
+        "l"(tm), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar), "l"(pol)
+        : "memory");
+}
 __device__ __forceinline__ void cp4(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -105,7 +122,7 @@ template <int N>
 __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-template <typename ST, int VEC, bool HV, int S>
+template <typename ST, int VEC, bool HV, int S, bool G4 = false>
 struct Ring {
     using L = Layout<ST, VEC, HV, S>;
     using K = prop::Kern<ST, VEC, 1, 32, HV>;
@@ -126,6 +143,7 @@ struct Ring {
     uint32_t pending = 0;   // bit s: stage s holds an issued, unsummed window
     bool dead = false;      // a wait ran out
     uint64_t pol_hot, pol_cold;
+    const CUtensorMap* tmap = nullptr;  // G4: the tensor map of T_in
     int lane;
 
     __device__ void setup(unsigned char* base, int lane_, bool partitioned) {
@@ -173,6 +191,28 @@ struct Ring {
         const int64_t kb = K0 + (int64_t)m * WIN;
         const int nvalid = (int)min((int64_t)WIN, K1 - kb);
         const uint32_t bar = bar0 + 8 * s;
+        if (G4) {  // 4-row tensor gathers; the staged metadata of every lane is read
+            __syncwarp();
+            const int ngroups = (nvalid + 3) / 4;
+            if (lane == 0) mbar_expect(bar, (uint32_t)(ngroups * 4 * ROW + ((a.test_wait_runout && m == 0) ? ROW : 0)));
+            __syncwarp();
+            if (lane < ngroups) {
+                const int base = (m % META) * WIN;
+                int32_t r[4];
+                int hot = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = 4 * lane + t;
+                    const int jj = j < nvalid ? j : 4 * lane;  // a group's tail repeats its first row
+                    r[t] = mcol[base + jj];
+                    if (a.hot_bits && j < nvalid) hot += (mword[base + jj] >> ((kb + jj) & 31)) & 1u;
+                }
+                gather4_rows(smem_addr(tring + s * L::STAGE + 4 * lane * ROW), tmap, r[0], r[1], r[2], r[3], bar,
+                             hot >= 2 ? pol_hot : pol_cold);
+            }
+            pending |= 1u << s;
+            return;
+        }
         // a.test_wait_runout (test hook): the first window of the warp expects one row more
         // than it copies, so its wait runs out and the error path is taken
         const int extra = (a.test_wait_runout && m == 0) ? ROW : 0;
@@ -343,14 +383,15 @@ struct ChunkCons {
     }
 };
 
-template <typename ST, int VEC, bool HV, int S>
-__global__ void __launch_bounds__(256, 1) k_ring(prop::Args a) {
-    using R = Ring<ST, VEC, HV, S>;
+template <typename ST, int VEC, bool HV, int S, bool G4>
+__global__ void __launch_bounds__(256, 1) k_ring(prop::Args a, const __grid_constant__ CUtensorMap tmap) {
+    using R = Ring<ST, VEC, HV, S, G4>;
     using L = typename R::L;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     R ring;
     ring.setup(smem + (size_t)warp * L::WARP_BYTES, lane, a.hot_bits != nullptr);
+    ring.tmap = &tmap;
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1ull);
@@ -378,17 +419,18 @@ __global__ void __launch_bounds__(256, 1) k_ring(prop::Args a) {
 }
 
 // Launch helpers (per storage type and vector width, in their own translation units).
-cudaError_t launch_f32_v8(const prop::Args& a, bool hv, int stages, int sms, cudaStream_t s, int* grid);
-cudaError_t launch_f32_v16(const prop::Args& a, bool hv, int stages, int sms, cudaStream_t s, int* grid);
-cudaError_t launch_bf16_v8(const prop::Args& a, bool hv, int stages, int sms, cudaStream_t s, int* grid);
-cudaError_t launch_bf16_v16(const prop::Args& a, bool hv, int stages, int sms, cudaStream_t s, int* grid);
+// tmap: NULL for one bulk copy per row, else the tensor map of T_in (4-row tensor gathers).
+cudaError_t launch_f32_v8(const prop::Args& a, const CUtensorMap* tmap, bool hv, int stages, int sms, cudaStream_t s, int* grid);
+cudaError_t launch_f32_v16(const prop::Args& a, const CUtensorMap* tmap, bool hv, int stages, int sms, cudaStream_t s, int* grid);
+cudaError_t launch_bf16_v8(const prop::Args& a, const CUtensorMap* tmap, bool hv, int stages, int sms, cudaStream_t s, int* grid);
+cudaError_t launch_bf16_v16(const prop::Args& a, const CUtensorMap* tmap, bool hv, int stages, int sms, cudaStream_t s, int* grid);
 
 // Warps per CTA and CTAs per SM for a per-warp footprint: as many warps as fit in the SM's
 // shared memory (up to 8 per CTA), one CTA per SM unless two fit.
-template <typename ST, int VEC, bool HV, int S>
-cudaError_t launch(const prop::Args& a, int sms, cudaStream_t st, int* grid_out) {
+template <typename ST, int VEC, bool HV, int S, bool G4>
+cudaError_t launch(const prop::Args& a, const CUtensorMap& tmap, int sms, cudaStream_t st, int* grid_out) {
     using L = Layout<ST, VEC, HV, S>;
-    auto kern = k_ring<ST, VEC, HV, S>;
+    auto kern = k_ring<ST, VEC, HV, S, G4>;
     int dev = 0, smem_max = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -405,18 +447,28 @@ cudaError_t launch(const prop::Args& a, int sms, cudaStream_t st, int* grid_out)
     if (per_sm < 1) per_sm = 1;
     const int grid = per_sm * sms;
     if (grid_out) *grid_out = grid;
-    kern<<<grid, warps * 32, bytes, st>>>(a);
+    kern<<<grid, warps * 32, bytes, st>>>(a, tmap);
     return cudaGetLastError();
 }
 
-template <typename ST, int VEC>
-cudaError_t launch_any(const prop::Args& a, bool hv, int stages, int sms, cudaStream_t s, int* grid) {
+template <typename ST, int VEC, bool G4>
+cudaError_t launch_stages(const prop::Args& a, const CUtensorMap& tm, bool hv, int stages, int sms, cudaStream_t s,
+                          int* grid) {
     switch (stages) {
-        case 2: return hv ? launch<ST, VEC, true, 2>(a, sms, s, grid) : launch<ST, VEC, false, 2>(a, sms, s, grid);
-        case 3: return hv ? launch<ST, VEC, true, 3>(a, sms, s, grid) : launch<ST, VEC, false, 3>(a, sms, s, grid);
-        case 4: return hv ? launch<ST, VEC, true, 4>(a, sms, s, grid) : launch<ST, VEC, false, 4>(a, sms, s, grid);
+        case 2: return hv ? launch<ST, VEC, true, 2, G4>(a, tm, sms, s, grid) : launch<ST, VEC, false, 2, G4>(a, tm, sms, s, grid);
+        case 3: return hv ? launch<ST, VEC, true, 3, G4>(a, tm, sms, s, grid) : launch<ST, VEC, false, 3, G4>(a, tm, sms, s, grid);
+        case 4: return hv ? launch<ST, VEC, true, 4, G4>(a, tm, sms, s, grid) : launch<ST, VEC, false, 4, G4>(a, tm, sms, s, grid);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <typename ST, int VEC>
+cudaError_t launch_any(const prop::Args& a, const CUtensorMap* tmap, bool hv, int stages, int sms, cudaStream_t s,
+                       int* grid) {
+    if (tmap) return launch_stages<ST, VEC, true>(a, *tmap, hv, stages, sms, s, grid);
+    CUtensorMap none;
+    memset(&none, 0, sizeof(none));
+    return launch_stages<ST, VEC, false>(a, none, hv, stages, sms, s, grid);
 }
 
 }  // namespace ring

@@ -1,6 +1,6 @@
-"""Shared-memory ring kernel (option staging = 2): gathered rows of T reach the sums through a
-warp-private ring filled by bulk copies, with a per-entry hot bitmap for the L2 policy instead
-of the hot-first row reorder.  Only the summation order differs from the register kernel, so
+"""Shared-memory ring kernel (option staging = 2: one bulk copy per gathered row; 3: TMA tensor
+gathers of 4 rows): gathered rows of T reach the sums through a warp-private ring, with a
+per-entry hot bitmap for the L2 policy instead of the hot-first row reorder.  Only the summation order differs from the register kernel, so
 
   * results stay within the FP32 / BF16 tolerances of the FP64 oracle (Algorithm 1) for every
     shape the ring covers (FP32 d = 64 and 128, BF16 d = 128 and 256), weighted and unit
@@ -44,10 +44,10 @@ def _graph(name):
     return _cache[name]
 
 
-def _run(e, d, storage, opts, iters=4, chunks=(4,)):
+def _run(e, d, storage, opts, iters=4, chunks=(4,), staging=2):
     import paper_2102_02302_gb300 as pkg
     with pkg.Context(0) as ctx:
-        ctx.set_option("staging", 2)
+        ctx.set_option("staging", staging)
         for k, v in opts.items():
             ctx.set_option(k, v)
         ctx.graph_build(e.src, e.dst, e.weights, e.directed)
@@ -81,23 +81,25 @@ def _check(g, out, d, storage, iters=4):
 SHAPES = [(64, "f32"), (128, "f32"), (128, "bf16"), (256, "bf16")]
 
 
+@pytest.mark.parametrize("staging", [2, 3])
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 @pytest.mark.parametrize("d,storage", SHAPES)
-def test_ring_matches_oracle(name, d, storage):
+def test_ring_matches_oracle(name, d, storage, staging):
     e, g = _graph(name)
     opts = {"split_len": 256} if name in ("star", "undirected_unit") else {}
-    (out,), hot, csr = _run(e, d, storage, opts)
+    (out,), hot, csr = _run(e, d, storage, opts, staging=staging)
     assert hot == 0  # T fits in L2: no hot bitmap
     assert np.array_equal(csr["rowptr"], g.rowptr) and np.array_equal(csr["col"], g.col)
     _check(g, out, d, storage)
 
 
+@pytest.mark.parametrize("staging", [2, 3])
 @pytest.mark.parametrize("stages", [2, 3, 4])
 @pytest.mark.parametrize("d,storage", [(128, "f32"), (128, "bf16")])
-def test_ring_stages_and_hot_bitmap(stages, d, storage):
+def test_ring_stages_and_hot_bitmap(stages, d, storage, staging):
     e, g = _graph("directed_weighted")
     opts = {"ring_stages": stages, "hot_bytes": 256 << 10, "split_len": 512}
-    (out,), hot, csr = _run(e, d, storage, opts)
+    (out,), hot, csr = _run(e, d, storage, opts, staging=staging)
     assert 0 < hot < g.nnz  # bitmap marks the entries of the hottest rows
     assert np.array_equal(csr["col"], g.col)  # rows keep ascending column order
     assert np.array_equal(csr["val"].view(np.uint32), g.val32.view(np.uint32))
@@ -119,13 +121,18 @@ def test_hot_set_is_the_exact_top_rows():
     assert above <= hot <= best
 
 
-def test_ring_deterministic_and_resumable():
+@pytest.mark.parametrize("staging", [2, 3])
+def test_ring_deterministic_and_resumable(staging):
     e, g = _graph("undirected_unit")
-    outs, _, _ = _run(e, 128, "bf16", {"hot_bytes": 64 << 10, "split_len": 256}, chunks=(2, 2))
-    outs4, _, _ = _run(e, 128, "bf16", {"hot_bytes": 64 << 10, "split_len": 256}, chunks=(4,))
-    again, _, _ = _run(e, 128, "bf16", {"hot_bytes": 64 << 10, "split_len": 256}, chunks=(4,))
+    opts = {"hot_bytes": 64 << 10, "split_len": 256}
+    outs, _, _ = _run(e, 128, "bf16", opts, chunks=(2, 2), staging=staging)
+    outs4, _, _ = _run(e, 128, "bf16", opts, chunks=(4,), staging=staging)
+    again, _, _ = _run(e, 128, "bf16", opts, chunks=(4,), staging=staging)
     assert np.array_equal(outs[1].view(np.uint32), outs4[0].view(np.uint32))
     assert np.array_equal(again[0].view(np.uint32), outs4[0].view(np.uint32))
+    if staging == 3:  # both issue modes fill the same slots: the same bits
+        bulk, _, _ = _run(e, 128, "bf16", opts, chunks=(4,), staging=2)
+        assert np.array_equal(bulk[0].view(np.uint32), outs4[0].view(np.uint32))
 
 
 def test_ring_and_register_kernels_agree():
@@ -144,11 +151,12 @@ def test_ring_and_register_kernels_agree():
     assert np.abs(res[1] - res[2]).max() <= 2e-6
 
 
-def test_ring_wait_that_runs_out_is_reported_and_context_stays_usable():
+@pytest.mark.parametrize("staging", [2, 3])
+def test_ring_wait_that_runs_out_is_reported_and_context_stays_usable(staging):
     import paper_2102_02302_gb300 as pkg
     e, g = _graph("undirected_unit")
     with pkg.Context(0) as ctx:
-        ctx.set_option("staging", 2)
+        ctx.set_option("staging", staging)
         ctx.graph_build(e.src, e.dst, e.weights, e.directed)
         ctx.init(128, 0, "f32")
         ctx.set_option("test_ring_wait", 1)
