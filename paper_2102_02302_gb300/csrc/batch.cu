@@ -95,58 +95,75 @@ __device__ __forceinline__ int find_graph(const int64_t* prefix, int count, int6
     return lo;
 }
 
+// Both passes below walk tiles of consecutive 16-byte vectors (coalesced), finding the graph
+// of a thread's first vector in the tile by binary search and then stepping forward.
+constexpr int64_t TILE_VECS = 4096;
+
+inline unsigned tile_grid(int64_t total, int sms) {
+    const int64_t tiles = (total + TILE_VECS - 1) / TILE_VECS;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 16));
+}
+
 // T_0 of every graph (16-byte vectors), same values as the single-graph init.
 __global__ void k_batch_init(const GDesc* gd, int count, const int64_t* vec_prefix,
                              const uint64_t* ids, unsigned char* TA) {
     const int64_t total = vec_prefix[count];
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < total;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int g = find_graph(vec_prefix, count, v);
-        const GDesc& G = gd[g];
-        const int64_t lv = v - vec_prefix[g];
-        const int vpr = G.row_bytes / 16;
-        const int64_t i = lv / vpr;
-        const int64_t jv = lv - i * vpr;
-        const uint64_t p = mix64(G.mseed ^ ids[G.node_off + i]);
-        uint4* dst = reinterpret_cast<uint4*>(TA + G.T_off) + lv;
-        if (G.dtype == CLEORA_F32) {
-            const uint32_t j = (uint32_t)jv * 4u;
-            *dst = make_uint4(__float_as_uint(init_value(p, j)), __float_as_uint(init_value(p, j + 1)),
-                              __float_as_uint(init_value(p, j + 2)), __float_as_uint(init_value(p, j + 3)));
-        } else {
-            const uint32_t j = (uint32_t)jv * 8u;
-            uint32_t w[4];
+    for (int64_t t0 = blockIdx.x * TILE_VECS; t0 < total; t0 += (int64_t)gridDim.x * TILE_VECS) {
+        const int64_t t1 = min(total, t0 + TILE_VECS);
+        if (t0 + threadIdx.x >= t1) continue;
+        int g = find_graph(vec_prefix, count, t0 + threadIdx.x);
+        for (int64_t v = t0 + threadIdx.x; v < t1; v += blockDim.x) {
+            while (vec_prefix[g + 1] <= v) ++g;
+            const GDesc& G = gd[g];
+            const int64_t lv = v - vec_prefix[g];
+            const int vpr = G.row_bytes / 16;
+            const int64_t i = lv / vpr;
+            const int64_t jv = lv - i * vpr;
+            const uint64_t p = mix64(G.mseed ^ ids[G.node_off + i]);
+            uint4* dst = reinterpret_cast<uint4*>(TA + G.T_off) + lv;
+            if (G.dtype == CLEORA_F32) {
+                const uint32_t j = (uint32_t)jv * 4u;
+                *dst = make_uint4(__float_as_uint(init_value(p, j)), __float_as_uint(init_value(p, j + 1)),
+                                  __float_as_uint(init_value(p, j + 2)), __float_as_uint(init_value(p, j + 3)));
+            } else {
+                const uint32_t j = (uint32_t)jv * 8u;
+                uint32_t w[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                __nv_bfloat162 h = __floats2bfloat162_rn(init_value(p, j + 2 * k), init_value(p, j + 2 * k + 1));
-                w[k] = *reinterpret_cast<uint32_t*>(&h);
+                for (int k = 0; k < 4; ++k) {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(init_value(p, j + 2 * k), init_value(p, j + 2 * k + 1));
+                    w[k] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                *dst = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            *dst = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
 
-// Final embeddings of every graph -> packed FP32 output (4 elements per thread-iteration).
+// Every graph's final iterate as FP32 into the packed output (4 elements per unit).
 __global__ void k_batch_out(const GDesc* gd, int count, const int64_t* outv_prefix,
                             const unsigned char* TA, const unsigned char* TB, float* out) {
     const int64_t total = outv_prefix[count];
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        const int g = find_graph(outv_prefix, count, u);
-        const GDesc& G = gd[g];
-        const int64_t e = (u - outv_prefix[g]) * 4;
-        const unsigned char* src = ((G.iters & 1) ? TB : TA) + G.T_off;
-        float4 o;
-        if (G.dtype == CLEORA_F32) {
-            o = *reinterpret_cast<const float4*>(src + e * 4);
-        } else {
-            const uint2 w = *reinterpret_cast<const uint2*>(src + e * 2);
-            o.x = __uint_as_float(w.x << 16);
-            o.y = __uint_as_float(w.x & 0xffff0000u);
-            o.z = __uint_as_float(w.y << 16);
-            o.w = __uint_as_float(w.y & 0xffff0000u);
+    for (int64_t t0 = blockIdx.x * TILE_VECS; t0 < total; t0 += (int64_t)gridDim.x * TILE_VECS) {
+        const int64_t t1 = min(total, t0 + TILE_VECS);
+        if (t0 + threadIdx.x >= t1) continue;
+        int g = find_graph(outv_prefix, count, t0 + threadIdx.x);
+        for (int64_t u = t0 + threadIdx.x; u < t1; u += blockDim.x) {
+            while (outv_prefix[g + 1] <= u) ++g;
+            const GDesc& G = gd[g];
+            const int64_t e = (u - outv_prefix[g]) * 4;
+            const unsigned char* src = ((G.iters & 1) ? TB : TA) + G.T_off;
+            float4 o;
+            if (G.dtype == CLEORA_F32) {
+                o = __ldcs(reinterpret_cast<const float4*>(src + e * 4));
+            } else {
+                const uint2 w = __ldcs(reinterpret_cast<const uint2*>(src + e * 2));
+                o.x = __uint_as_float(w.x << 16);
+                o.y = __uint_as_float(w.x & 0xffff0000u);
+                o.z = __uint_as_float(w.y << 16);
+                o.w = __uint_as_float(w.y & 0xffff0000u);
+            }
+            __stcs(reinterpret_cast<float4*>(out + G.out_off + e), o);
         }
-        *reinterpret_cast<float4*>(out + G.out_off + e) = o;
     }
 }
 
@@ -421,7 +438,7 @@ int enqueue(cleora_batch* b, Packed& pk, bool init, int s0, int s1, bool out, in
                                     sizeof(unsigned long long) * (pk.fams.size() * (pk.max_iters + 1) + 1), s);
     if (e != cudaSuccess) return from_ctx(b, cuda_fail(c, e, "counter reset", __FILE__, __LINE__));
     if (init && pk.T_bytes > 0) {
-        k_batch_init<<<grid_for(pk.T_bytes / 16, 256, sms), 256, 0, s>>>(pk.gd, pk.count, pk.vec_prefix, pk.ids, pk.TA);
+        k_batch_init<<<tile_grid(pk.T_bytes / 16, sms), 256, 0, s>>>(pk.gd, pk.count, pk.vec_prefix, pk.ids, pk.TA);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return from_ctx(b, cuda_fail(c, e, "batch init", __FILE__, __LINE__));
     }
@@ -477,7 +494,7 @@ int enqueue(cleora_batch* b, Packed& pk, bool init, int s0, int s1, bool out, in
             return from_ctx(b, cuda_fail(c, e, "join", __FILE__, __LINE__));
     }
     if (out && pk.total_out > 0) {
-        k_batch_out<<<grid_for(pk.total_out / 4, 256, sms), 256, 0, s>>>(pk.gd, pk.count, pk.outv_prefix, pk.TA,
+        k_batch_out<<<tile_grid(pk.total_out / 4, sms), 256, 0, s>>>(pk.gd, pk.count, pk.outv_prefix, pk.TA,
                                                                          pk.TB, pk.out);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return from_ctx(b, cuda_fail(c, e, "batch output", __FILE__, __LINE__));
@@ -518,15 +535,21 @@ int autotune(cleora_batch* b) {
         std::vector<int>& members = kv.second;
         std::vector<Shape> cands = candidates(d, (cleora_dtype)dt);
         if (cands.size() < 2) continue;
-        // sample: up to 64 graphs spread over the class's sizes, at most ~16M entries
+        // sample: graphs spread over the class's sizes holding up to 200M entries -- the whole
+        // class when it is smaller -- so that its embeddings, like the batch's, outgrow L2 and
+        // the candidates are timed in the memory regime they will run in
         std::vector<int> byn(members);
         std::sort(byn.begin(), byn.end(), [&](int x, int y) { return b->graphs[x].nnz < b->graphs[y].nnz; });
         std::vector<int> sample;
-        const int want = std::min<int>(64, (int)byn.size());
+        int64_t class_nnz = 0;
+        for (int i : byn) class_nnz += b->graphs[i].nnz;
+        const int64_t cap = 200000000;
+        const int want = class_nnz <= cap ? (int)byn.size()
+                                          : std::max<int>(1, (int)((double)byn.size() * cap / class_nnz));
         int64_t nnz_sum = 0;
         for (int k = 0; k < want; ++k) {
             const int idx = byn[(size_t)k * byn.size() / want];
-            if (nnz_sum > 16000000 && !sample.empty()) break;
+            if (nnz_sum > cap && !sample.empty()) break;
             sample.push_back(idx);
             nnz_sum += b->graphs[idx].nnz;
         }
