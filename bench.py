@@ -55,6 +55,10 @@ CPU_SAMPLES = {
 CPU_SAMPLES["large_1_40"] = CPU_SAMPLES["large"]
 
 
+STAGING_LABELS = {0: "automatic", 1: "registers", 2: "ring (bulk copy per row)",
+                  3: "ring (4-row tensor gathers)"}
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -768,7 +772,7 @@ def main():
     ap.add_argument("--storage", default="both", choices=["both", "bf16", "f32"])
     ap.add_argument("--hot-bytes", type=int, default=0,
                     help="L2 bytes kept for hot rows (0: library default, 1: off)")
-    ap.add_argument("--staging", type=int, default=0,
+    ap.add_argument("--staging", type=int, default=0, choices=sorted(STAGING_LABELS),
                     help="gathered rows reach the sums through 0: automatic, 1: registers, 2: the shared-memory ring")
     ap.add_argument("--ring-stages", type=int, default=0, help="ring stages (0: library default)")
     ap.add_argument("--no-batch", action="store_true")
@@ -933,7 +937,7 @@ def main():
                    "step": "graph build + init + I iterations on device-resident edges",
                    "value_def": "nnz*d / median per-iteration time (CUDA events)",
                    "hot_bytes": args.hot_bytes or "default",
-                   "staging": {0: "automatic", 1: "registers", 2: "ring"}[args.staging],
+                   "staging": STAGING_LABELS[args.staging],
                    "ring_stages": args.ring_stages or "default",
                    "generator_s": gen_s},
         "roofline": hs["roofline"],

@@ -33,3 +33,13 @@ def test_traffic_entries_are_tied_to_the_kernel_sources(tmp_path, monkeypatch):
     assert bench.measured_traffic("large/f32") is None  # taken on another kernel build
     assert bench.measured_traffic("mid/bf16") is None
     assert os.path.exists(os.path.join(real_root, "profiles", "traffic.json"))
+
+
+def test_every_staging_option_has_a_label():
+    import paper_2102_02302_gb300 as pkg
+    import re
+    header = open(os.path.join(bench.ROOT, "include", "cleora.h")).read()
+    doc = header[header.index("CLEORA_OPT_STAGING"):header.index("CLEORA_OPT_RING_STAGES")]
+    values = {int(v) for v in re.findall(r"(\d) = ", doc)} | {0, 1}
+    assert values <= set(bench.STAGING_LABELS)
+    assert pkg.cleora.OPTIONS["staging"] == 7
