@@ -573,52 +573,26 @@ class PinnedArena:
 
 
 def serve_run(srv, pool, arena, jobs, arrivals, start):
-    """Feeds jobs at their arrival times and collects them in completion order.  A job whose
-    FP32 output does not fit in the pinned arena yet waits beside the feed, so later jobs that
-    fit are still submitted on time; once the oldest waiting job has waited a second, later
-    jobs stop passing it.  Latency counts from the arrival time either way.  Returns per-job
-    results in job order."""
+    """Feeds jobs at their arrival times (waiting for output space when the arena is full)
+    and collects them in completion order.  Returns per-job results in job order."""
     import threading
     ids, regions, out = {}, {}, {}
     lock = threading.Lock()
 
-    def submit(k, reg):
-        g, d, it, st = jobs[k]
-        p = pool[g]
-        buf = arena.view(reg[0], p["n"], d)
-        jid = srv.submit(p["src"], p["dst"], None, False, d, it, 1000 + k, st, buf, nodes_hint=p["n"])
-        with lock:
-            ids[jid] = k
-            regions[jid] = reg
-
     def feeder():
-        waiting = []  # arrived jobs without output space, in arrival order
-        k = 0
-        while k < len(jobs) or waiting:
-            now = srv.now()
-            while k < len(jobs) and start + arrivals[k] <= now:
-                waiting.append(k)
-                k += 1
-            still = []
+        for k, (g, d, it, st) in enumerate(jobs):
+            delay = start + arrivals[k] - srv.now()
+            if delay > 0:
+                time.sleep(delay)
+            p = pool[g]
             with arena.cv:
-                for pos, j in enumerate(waiting):
-                    if still and now - (start + arrivals[still[0]]) > 1.0:
-                        still.extend(waiting[pos:])  # the oldest waiter keeps its place
-                        break
-                    g, d = jobs[j][0], jobs[j][1]
-                    reg = arena.alloc(pool[g]["n"] * d * 4)
-                    if reg is None:
-                        still.append(j)
-                    else:
-                        submit(j, reg)
-                waiting = still
-                nxt = start + arrivals[k] - now if k < len(jobs) else 0.05
-                if waiting:
-                    arena.cv.wait(max(1e-4, min(0.05, nxt)))
-            if not waiting and k < len(jobs):
-                delay = start + arrivals[k] - srv.now()
-                if delay > 0:
-                    time.sleep(delay)
+                while (reg := arena.alloc(p["n"] * d * 4)) is None:
+                    arena.cv.wait(0.05)
+            buf = arena.view(reg[0], p["n"], d)
+            jid = srv.submit(p["src"], p["dst"], None, False, d, it, 1000 + k, st, buf, nodes_hint=p["n"])
+            with lock:
+                ids[jid] = k
+                regions[jid] = reg
 
     th = threading.Thread(target=feeder)
     th.start()
@@ -637,7 +611,7 @@ def serve_run(srv, pool, arena, jobs, arrivals, start):
 
 
 def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0,
-                  arena_bytes=48 << 30):
+                  arena_bytes=96 << 30):
     import paper_2102_02302_gb300 as pkg
     t = time.perf_counter()
     pool = serve_pool(seed=seed)
@@ -799,7 +773,7 @@ def main():
     ap.add_argument("--hot-bytes", type=int, default=0,
                     help="L2 bytes kept for hot rows (0: library default, 1: off)")
     ap.add_argument("--staging", type=int, default=0, choices=sorted(STAGING_LABELS),
-                    help="gathered rows reach the sums through 0: automatic, 1: registers, 2: the shared-memory ring")
+                    help="gathered rows reach the sums through 0: automatic, 1: registers, 2: the shared-memory ring (a bulk copy per row), 3: the ring (4-row tensor gathers)")
     ap.add_argument("--ring-stages", type=int, default=0, help="ring stages (0: library default)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")

@@ -44,7 +44,6 @@ struct Family {
     BTask* tasks = nullptr;
     int64_t ntasks = 0;
     std::vector<int64_t> nt_step;  // nt_step[s]: tasks of graphs with iters >= s
-    std::vector<double> w_step;    // w_step[s]: their gathered bytes (nnz x row bytes)
 };
 
 struct Packed {
@@ -415,17 +414,10 @@ int pack(cleora_batch* b, const std::vector<int>& which, Packed& pk) {
         nnz_off += og.nnz;
     }
     // tasks still active at step s: slots are sorted by iters, so count per family
-    for (Family& f : pk.fams) {
-        f.nt_step.assign(pk.max_iters + 1, 0);
-        f.w_step.assign(pk.max_iters + 1, 0.0);
-    }
+    for (Family& f : pk.fams) f.nt_step.assign(pk.max_iters + 1, 0);
     for (int k = 0; k < pk.count; ++k) {
         const OneGraph& og = b->graphs[order[k]];
-        Family& f = pk.fams[pk.hgd[k].family];
-        for (int st = 1; st <= og.iters; ++st) {
-            f.nt_step[st] += og.ntasks;
-            f.w_step[st] += (double)og.nnz * pk.hgd[k].row_bytes;
-        }
+        for (int st = 1; st <= og.iters; ++st) pk.fams[pk.hgd[k].family].nt_step[st] += og.ntasks;
     }
     PKC(cudaMemcpyAsync(pk.gd, pk.hgd.data(), sizeof(GDesc) * pk.count, cudaMemcpyHostToDevice, s));
     PKC(cudaMemcpyAsync(pk.vec_prefix, vecp.data(), 8 * vecp.size(), cudaMemcpyHostToDevice, s));
@@ -471,8 +463,6 @@ int enqueue(cleora_batch* b, Packed& pk, bool init, int s0, int s1, bool out, in
         if ((e = cudaStreamWaitEvent(b->fstreams[f], b->fork, 0)) != cudaSuccess)
             return from_ctx(b, cuda_fail(c, e, "fork", __FILE__, __LINE__));
     for (int st = s0; st <= s1; ++st) {
-        double step_work = 0.0;
-        for (const Family& fam : pk.fams) step_work += fam.w_step[st];
         for (size_t f = 0; f < pk.fams.size(); ++f) {
             const Family& fam = pk.fams[f];
             if (fam.nt_step[st] == 0) continue;
@@ -493,7 +483,6 @@ int enqueue(cleora_batch* b, Packed& pk, bool init, int s0, int s1, bool out, in
             ba.err = c->err_flag;
             ba.step = st;
             ba.hv = fam.hv;
-            ba.share = step_work > 0.0 ? (float)(fam.w_step[st] / step_work) : 1.f;
             ++nl;
             if ((e = launch_family(fam, ba, sms, b->fstreams[f])) != cudaSuccess)
                 return from_ctx(b, cuda_fail(c, e, "batch step", __FILE__, __LINE__));

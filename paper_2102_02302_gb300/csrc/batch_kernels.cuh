@@ -54,7 +54,6 @@ struct BatchArgs {
     int* err;
     int step;  // 1-based; odd steps read TA and write TB
     int hv;    // the family's graphs have per-entry values
-    float share;  // fraction of the device's CTA slots this launch takes (families run side by side)
 };
 
 constexpr int variant_of(int G, int mode, bool hv) {
@@ -142,13 +141,8 @@ struct BatchLaunch {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0);
         if (e != cudaSuccess) return e;
         if (bps < 1) bps = 1;
-        // the family's share of the step's gathered bytes sets its share of the CTA slots, so
-        // the launches of one step fit on the device side by side
-        int ctas = (int)((double)bps * sms * (ba.share > 0.f ? ba.share : 1.f) + 0.999);
-        if (ctas < 1) ctas = 1;
-        if (ctas > bps * sms) ctas = bps * sms;
-        if (grid) *grid = ctas;
-        kern<<<ctas, 256, 0, s>>>(ba);
+        if (grid) *grid = bps * sms;
+        kern<<<bps * sms, 256, 0, s>>>(ba);
         return cudaGetLastError();
     }
     static cudaError_t run(int cpl, int G, int mode, const BatchArgs& ba, int sms, cudaStream_t s, int* grid) {
