@@ -480,42 +480,6 @@ struct Kern {
         }
     }
 
-    // Column (and value) window [cb, cb + 32) into the lanes' registers.  When the previous
-    // window was [cb - 32, cb), its load already started a copy of this one into the warp's
-    // shared-memory slot (4-byte cp.async per lane: each lane copies and reads only its own
-    // entry); otherwise the window comes straight from global memory.  Either way the copy of
-    // [cb + 32, cb + 64) is started, so the next switch need not wait for DRAM.  Entries at or
-    // past `limit` read as 0.
-    __device__ static __forceinline__ void load_window(const Args& a, int64_t cb, bool adjacent, int64_t limit,
-                                                       int lane, int& mc, float& mw) {
-        __shared__ int32_t s_col[8 * 32];
-        __shared__ float s_val[HV ? 8 * 32 : 1];
-        const int slot = (threadIdx.x >> 5) * 32 + lane;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        if (adjacent) {
-            mc = s_col[slot];
-            if (HV) mw = s_val[slot];
-        } else {
-            mc = 0;
-            mw = 0.f;
-            if (cb + lane < limit) {
-                mc = __ldcs(a.col + cb + lane);
-                if (HV) mw = __ldcs(a.val + cb + lane);
-            }
-        }
-        const int64_t kn = cb + 32 + lane;
-        const int nb = kn < limit ? 4 : 0;  // source bytes: 0 fills the slot with zeros
-        const int64_t ks = kn < limit ? kn : 0;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(s_col + slot)),
-                     "l"(a.col + ks), "r"(nb) : "memory");
-        if (HV)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(s_val + slot)),
-                         "l"(a.val + ks), "r"(nb) : "memory");
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    // No copy stays in flight when a row loop returns.
-    __device__ static __forceinline__ void windows_done() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
     // Accumulate entries [k0, k1) with the whole warp (groups interleave entries).
     __device__ static __forceinline__ void range_coop(const Args& a, Acc& acc, int64_t k0, int64_t k1,
                                                       int64_t hot_end, int lane, int g, int lg) {
@@ -525,9 +489,14 @@ struct Kern {
         float mw = 0.f;
         for (int64_t k = k0; k < k1;) {
             if (k >= cb + 32) {
-                const bool adjacent = k == cb + 32;
                 cb = k;
-                load_window(a, cb, adjacent, k1, lane, mc, mw);
+                const int m = (int)min((int64_t)32, k1 - cb);
+                mc = 0;
+                mw = 0.f;
+                if (lane < m) {
+                    mc = __ldcs(a.col + cb + lane);
+                    if (HV) mw = __ldcs(a.val + cb + lane);
+                }
             }
             // a segment ends at the window's end, the range's end or the row's hot boundary
             const bool hot = k < hot_end;
@@ -537,7 +506,6 @@ struct Kern {
             acc.flush();
             k = cb + jh;
         }
-        windows_done();
     }
 
     // Mode 1: the warp walks rows [rb, re) one at a time; rowptr and column windows are
@@ -575,9 +543,13 @@ struct Kern {
             }
             for (int64_t k = beg; k < end;) {
                 if (k < cb || k >= cb + 32) {
-                    const bool adjacent = k == cb + 32;
                     cb = k;
-                    load_window(a, cb, adjacent, a.nnz, lane, mc, mw);
+                    mc = 0;
+                    mw = 0.f;
+                    if (cb + lane < a.nnz) {
+                        mc = __ldcs(a.col + cb + lane);
+                        if (HV) mw = __ldcs(a.val + cb + lane);
+                    }
                 }
                 // a segment ends at the window's end, the row's end or its hot boundary
                 const bool hot = k < hot_end;
@@ -590,7 +562,6 @@ struct Kern {
             reduce_groups(acc);
             finish_row(a, acc, r, lg, g == 0, FULL);
         }
-        windows_done();
     }
 
     // Mode 2: lane group g owns rows rb + g, rb + g + P, ...
