@@ -611,13 +611,14 @@ def serve_run(srv, pool, arena, jobs, arrivals, start):
 
 
 def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0,
-                  arena_bytes=96 << 30):
+                  arena_bytes=96 << 30, short_slots=2, short_job_s=0.02, task_quantum=0):
     import paper_2102_02302_gb300 as pkg
     t = time.perf_counter()
     pool = serve_pool(seed=seed)
     arena = PinnedArena(arena_bytes)
     gen_s = time.perf_counter() - t
-    with pkg.Server(device, max_slots=slots) as srv:
+    with pkg.Server(device, max_slots=slots, short_slots=short_slots, short_job_seconds=short_job_s,
+                    task_quantum=task_quantum) as srv:
         # capacity: closed loop (every job available at once; output space is the only gate)
         cap_jobs = serve_jobs(pool, n_capacity, seed + 1)
         t0 = srv.now()
@@ -651,16 +652,24 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
         if sel.size:
             by_size.append({"class": f"work quartile {c + 1}", "jobs": int(sel.size),
                             "p50_ms": float(np.percentile(sel, 50) * 1e3),
-                            "p99_ms": float(np.percentile(sel, 99) * 1e3)})
-    return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "failed": n_jobs - len(ok),
+                            "p99_ms": float(np.percentile(sel, 99) * 1e3),
+                            "queue_wait_p99_ms": float(np.percentile(wait[cls == c], 99) * 1e3),
+                            "service_p50_ms": float(np.percentile(svc[cls == c], 50) * 1e3),
+                            "service_p99_ms": float(np.percentile(svc[cls == c], 99) * 1e3)})
+    return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "short_slots": short_slots,
+            "short_job_s": short_job_s, "task_quantum": 1 if task_quantum == 0 else max(0, task_quantum),
+            "failed": n_jobs - len(ok),
             "capacity_jobs_per_s": capacity, "lambda_jobs_per_s": lam,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "queue_wait_p50_ms": float(np.percentile(wait, 50) * 1e3),
+            "queue_wait_p99_ms": float(np.percentile(wait, 99) * 1e3),
             "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
             "service_p99_ms": float(np.percentile(svc, 99) * 1e3),
             "by_size": by_size,
             "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
-            "admission": "earliest virtual finish (arrival + estimated service) among jobs that fit the budget",
+            "admission": "earliest virtual finish (arrival + estimated service) among jobs that fit the budget; "
+                         "short jobs (estimated service <= short_job_s) also on short slots with their own "
+                         "reserve, on high-priority streams",
             "p99_ms_largest_10pct": float(np.percentile(lat[big >= q], 99) * 1e3),
             "p99_ms_other_90pct": float(np.percentile(lat[big < q], 99) * 1e3),
             "jobs_per_s": (n_jobs - warm) / span, "nnz_d_iters_per_s": work / span,
@@ -780,6 +789,9 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 10k-node and 2M-node workloads (GPU and full oracle runs)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-short-slots", type=int, default=2, help="serving slots for short jobs only")
+    ap.add_argument("--serve-quantum", type=int, default=0,
+                    help="tasks per warp before a propagate CTA retires (0: 1, -1: persistent)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-autotune", type=int, default=1, help="1: autotuned schedules, 0: defaults")
     args = ap.parse_args()
@@ -789,7 +801,8 @@ def main():
         import torch
         rank, local_rank, world = env_rank()
         torch.cuda.set_device(local_rank)
-        r = serve_measure(local_rank, args.serve_jobs)
+        r = serve_measure(local_rank, args.serve_jobs, short_slots=args.serve_short_slots,
+                          task_quantum=args.serve_quantum)
         if rank == 0:
             print(json.dumps({"metric": "job p50/p99 latency", "value": r["p99_ms"], "unit": "ms",
                               "n_gpus": world, "steps": args.serve_jobs, "warmup": r["warmup_jobs"],
@@ -917,7 +930,8 @@ def main():
 
     serving = None
     if not args.no_serve:
-        serving = serve_measure(device, args.serve_jobs)
+        serving = serve_measure(device, args.serve_jobs, short_slots=args.serve_short_slots,
+                                task_quantum=args.serve_quantum)
 
     configs = None
     if not args.no_configs and rank == 0 and world == 1:

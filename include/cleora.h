@@ -168,9 +168,16 @@ typedef enum {
                                     returns CLEORA_ERR_DEVICE), waits again (bounded) and
                                     returns, leaving the context usable.  The results of
                                     that launch are not valid                              */
-    CLEORA_OPT_CHUNK_BYTES = 10  /* device bytes one chunk of cleora_chunked_embed may use
+    CLEORA_OPT_CHUNK_BYTES = 10, /* device bytes one chunk of cleora_chunked_embed may use
                                     when the library picks the chunks; 0 = 80% of the free
                                     device memory at the call                              */
+    CLEORA_OPT_TASK_QUANTUM = 11 /* tasks a warp of the propagate kernel takes before it
+                                    exits (0..2^20); 0 = a persistent grid whose warps run
+                                    until the task queue is empty.  With a quantum the grid
+                                    has one CTA per 8 x quantum tasks, so CTAs retire during
+                                    the launch and kernels on other (higher-priority)
+                                    streams get SMs in between.  Results are the same bits
+                                    for any value (tasks and their sums do not change)     */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
@@ -332,6 +339,15 @@ typedef struct {
     int queue_capacity;        /* waiting jobs accepted; 0: unbounded                       */
     int inject_alloc_failure_every; /* test hook: every k-th admitted job gets a failing
                                        allocation (reported as CLEORA_ERR_OOM); 0: off      */
+    int short_slots;           /* further slots (0..64) that take short jobs only, from a
+                                  reserve of their own: min(2 GiB per slot, 1/8 of the
+                                  budget), set aside from the budget; 0: none               */
+    double short_job_seconds;  /* a job is short when its estimated service time is at most
+                                  this; short jobs run on a high-priority stream in any
+                                  slot; 0: 0.02 s                                          */
+    int task_quantum;          /* CLEORA_OPT_TASK_QUANTUM of the slots' contexts: 0 = 1 (a
+                                  long job's propagate CTAs retire after one task per warp,
+                                  so short jobs' kernels get SMs); -1 = persistent grids    */
 } cleora_server_config;
 
 typedef struct {
@@ -365,10 +381,12 @@ typedef struct {
  * plus an estimated service time (a cost model of its host transfers, graph build and
  * gathered bytes), so short jobs go ahead of long ones while a job is only passed by jobs
  * that arrived within its own service estimate after it.  A job passed over 8 times because
- * it did not fit stops later jobs from passing it.  Jobs on different slots overlap on the GPU.  After
+ * it did not fit stops later jobs from passing it.  A short_slots slot takes the earliest short
+ * job that fits its reserve.  Jobs on different slots overlap on the GPU.  After
  * a job, its slot returns the memory it held to the driver (pool trim) except a cache of
- * min(1 GiB, budget / (8 slots)) per slot, which is set aside from the budget, so the budget
- * tracks what running jobs and the slot caches hold. */
+ * min(1 GiB, budget / (8 x all slots)) per slot, which is set aside from the budget, so the
+ * budget tracks what running jobs and the slot caches hold.  cleora_serve_stats reports the
+ * general budget and the short reserve together. */
 int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg);
 /* Queues a job; *job_id identifies it.  CLEORA_ERR_REJECTED: its estimate exceeds the whole
  * budget, or the queue is full.  CLEORA_ERR_INVALID_ARG: a malformed job. */

@@ -6,9 +6,16 @@
 // gathered bytes) -- among those whose estimated peak device bytes fit in the budget beside
 // the running jobs' reservations.  Short jobs thus go ahead of long ones, but a job is only
 // passed by jobs that arrived less than its own service estimate after it, so every job
-// progresses; and a job passed over 8 times for lack of memory blocks further passing.  A job runs the whole method on its slot's stream (upload
-// and build, init, iterations, FP32 result to host), so jobs on different slots overlap on
-// the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver down
+// progresses; and a job passed over 8 times for lack of memory blocks further passing.
+//
+// Short jobs (estimated service at most short_job_seconds) also have short_slots slots of
+// their own, with a memory reserve of their own, so they never wait for a long job to leave a
+// slot; and every short job runs on a high-priority stream.  Propagate launches retire their
+// CTAs after a quantum of tasks, so a short job's kernels get SMs within about one task of a
+// long job's, instead of after the whole launch.
+//
+// A job runs the whole method on a stream of its slot (upload and build, init, iterations,
+// FP32 result to host), so jobs on different slots overlap on the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver down
 // to a small per-slot cache (charged to the budget up front), and returns the reservation;
 // waiting workers are woken and admission runs again.
 //
@@ -39,6 +46,8 @@ struct Job {
     int64_t est = 0;       // estimated peak device bytes
     double key = 0.0;      // arrival + estimated service seconds: admission order
     int bypassed = 0;
+    bool is_short = false;     // estimated service at most the server's short_job_seconds
+    bool on_short_slot = false;
     JobState state = WAITING;
     cleora_result res;
 };
@@ -62,7 +71,11 @@ double service_estimate(const cleora_job& j) {
 
 struct cleora_server {
     cleora_server_config cfg;
-    int64_t budget = 0;      // for running jobs' reservations
+    int64_t budget = 0;      // for running jobs' reservations (general slots)
+    int64_t short_budget = 0;   // the short slots' own reserve
+    int64_t reserved_short = 0;
+    double short_s = 0.02;      // service estimate at or below which a job is short
+    std::vector<cudaStream_t> hi, lo;  // per slot: high- and low-priority streams
     int64_t slot_cache = 0;  // device bytes each slot's pool may keep between jobs
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
@@ -113,34 +126,49 @@ int run_job(cleora_server* s, cleora_ctx* ctx, Job& job) {
 
 void worker_main(cleora_server* s, int slot) {
     cleora_ctx* ctx = s->slots[slot];
+    const bool short_slot = slot >= s->cfg.max_slots;
     for (;;) {
         std::shared_ptr<Job> job;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
                 if (s->stop) return;
-                // earliest virtual finish that fits; a job passed over too often for lack of
-                // memory stops the scan (its turn comes when memory is returned)
                 std::stable_sort(s->queue.begin(), s->queue.end(),
                                  [](const std::shared_ptr<Job>& x, const std::shared_ptr<Job>& y) {
                                      return x->key < y->key;
                                  });
-                for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
-                    if (s->reserved + (*it)->est <= s->budget) {
-                        job = *it;
-                        s->queue.erase(it);
+                if (short_slot) {
+                    // the earliest short job that fits the short reserve (the general slots'
+                    // memory is not touched, so no job's bypass count moves)
+                    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                        if ((*it)->is_short && s->reserved_short + (*it)->est <= s->short_budget) {
+                            job = *it;
+                            s->queue.erase(it);
+                            break;
+                        }
+                    }
+                    if (job) break;
+                } else {
+                    // earliest virtual finish that fits; a job passed over too often for lack
+                    // of memory stops the scan (its turn comes when memory is returned)
+                    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                        if (s->reserved + (*it)->est <= s->budget) {
+                            job = *it;
+                            s->queue.erase(it);
+                            break;
+                        }
+                        if ((*it)->bypassed >= MAX_BYPASS) break;
+                    }
+                    if (job) {
+                        for (auto& q : s->queue)  // every job ahead of it did not fit
+                            if (q->key < job->key) q->bypassed++;
                         break;
                     }
-                    if ((*it)->bypassed >= MAX_BYPASS) break;
-                }
-                if (job) {
-                    for (auto& q : s->queue)  // every job ahead of it did not fit
-                        if (q->key < job->key) q->bypassed++;
-                    break;
                 }
                 s->cv_work.wait(lk);
             }
-            s->reserved += job->est;
+            job->on_short_slot = short_slot;
+            (short_slot ? s->reserved_short : s->reserved) += job->est;
             s->running += 1;
             s->admitted += 1;
             job->state = RUNNING;
@@ -150,6 +178,9 @@ void worker_main(cleora_server* s, int slot) {
             const int k = s->cfg.inject_alloc_failure_every;
             ctx->inject_alloc_fail = (k > 0 && s->admitted % k == 0) ? 0 : -1;
         }
+        // the slot's previous job ended with a synchronize of its stream, so the context can
+        // move to the other stream
+        ctx->stream = job->is_short ? s->hi[slot] : s->lo[slot];
         int st = run_job(s, ctx, *job);
         ctx->inject_alloc_fail = -1;
         {
@@ -165,7 +196,7 @@ void worker_main(cleora_server* s, int slot) {
             job->res.t_done = s->now();
             job->state = DONE;
             s->finished.push_back(job->id);
-            s->reserved -= job->est;
+            (job->on_short_slot ? s->reserved_short : s->reserved) -= job->est;
             s->running -= 1;
             s->completed += 1;
         }
@@ -210,13 +241,18 @@ int64_t cleora_serve_estimate(const cleora_job* j) {
 }
 
 int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
-    if (!out || !cfg || cfg->max_slots < 0 || cfg->queue_capacity < 0 || cfg->hbm_budget_bytes < 0)
+    if (!out || !cfg || cfg->max_slots < 0 || cfg->queue_capacity < 0 || cfg->hbm_budget_bytes < 0 ||
+        cfg->short_slots < 0 || cfg->short_slots > 64 || !(cfg->short_job_seconds >= 0.0) ||
+        cfg->task_quantum < -1 || cfg->task_quantum > (1 << 20))
         return CLEORA_ERR_INVALID_ARG;
     *out = nullptr;
     cleora_server* s = new (std::nothrow) cleora_server();
     if (!s) return CLEORA_ERR_OOM;
     s->cfg = *cfg;
     if (s->cfg.max_slots == 0) s->cfg.max_slots = 4;
+    if (s->cfg.short_job_seconds > 0.0) s->short_s = s->cfg.short_job_seconds;
+    const int all_slots = s->cfg.max_slots + s->cfg.short_slots;
+    const int quantum = s->cfg.task_quantum == 0 ? 1 : std::max(0, s->cfg.task_quantum);
     s->t0 = std::chrono::steady_clock::now();
     {
         DeviceGuard guard(cfg->device);
@@ -232,21 +268,42 @@ int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
         }
         const int64_t total = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes : (int64_t)(free_b / 10 * 8);
         // each slot keeps up to slot_cache bytes of its pool between jobs (small jobs then
-        // reuse it without new mappings); those bytes come out of the budget
-        s->slot_cache = std::min<int64_t>((int64_t)1 << 30, total / (8 * (int64_t)s->cfg.max_slots));
-        s->budget = total - s->slot_cache * s->cfg.max_slots;
+        // reuse it without new mappings); those bytes come out of the budget, and so does the
+        // short slots' reserve (2 GiB each, at most an eighth of the total)
+        s->slot_cache = std::min<int64_t>((int64_t)1 << 30, total / (8 * (int64_t)all_slots));
+        s->short_budget = std::min<int64_t>(total / 8, (int64_t)s->cfg.short_slots << 31);
+        s->budget = total - s->slot_cache * all_slots - s->short_budget;
     }
-    for (int k = 0; k < s->cfg.max_slots; ++k) {
-        cleora_ctx* c = nullptr;
-        int rc = cleora_create(&c, cfg->device, nullptr);
-        if (rc != CLEORA_OK) {
-            for (cleora_ctx* x : s->slots) cleora_destroy(x);
-            delete s;
-            return rc;
+    int lo_prio = 0, hi_prio = 0;  // numerically lower is higher priority
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    int rc = CLEORA_OK;
+    for (int k = 0; k < all_slots && rc == CLEORA_OK; ++k) {
+        DeviceGuard guard(cfg->device);
+        cudaStream_t h = nullptr, l = nullptr;
+        if (cudaStreamCreateWithPriority(&h, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&l, cudaStreamNonBlocking, lo_prio) != cudaSuccess) {
+            cudaGetLastError();
+            if (h) cudaStreamDestroy(h);
+            rc = CLEORA_ERR_CUDA;
+            break;
         }
-        s->slots.push_back(c);
+        s->hi.push_back(h);
+        s->lo.push_back(l);
+        cleora_ctx* c = nullptr;
+        rc = cleora_create(&c, cfg->device, l);
+        if (rc == CLEORA_OK) {
+            s->slots.push_back(c);
+            rc = cleora_set_option(c, CLEORA_OPT_TASK_QUANTUM, quantum);
+        }
     }
-    for (int k = 0; k < s->cfg.max_slots; ++k) s->workers.emplace_back(worker_main, s, k);
+    if (rc != CLEORA_OK) {
+        for (cleora_ctx* x : s->slots) cleora_destroy(x);
+        for (cudaStream_t x : s->hi) cudaStreamDestroy(x);
+        for (cudaStream_t x : s->lo) cudaStreamDestroy(x);
+        delete s;
+        return rc;
+    }
+    for (int k = 0; k < all_slots; ++k) s->workers.emplace_back(worker_main, s, k);
     *out = s;
     return CLEORA_OK;
 }
@@ -256,17 +313,19 @@ int cleora_serve_submit(cleora_server* s, const cleora_job* job, uint64_t* job_i
     auto j = std::make_shared<Job>();
     j->spec = *job;
     j->est = cleora_serve_estimate(job);
+    const double svc = service_estimate(*job);
     j->res = cleora_result();
     j->res.slot = -1;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return CLEORA_ERR_STATE;
-        if (j->est > s->budget) return CLEORA_ERR_REJECTED;
+        j->is_short = svc <= s->short_s;
+        if (j->est > s->budget && !(j->is_short && j->est <= s->short_budget)) return CLEORA_ERR_REJECTED;
         if (s->cfg.queue_capacity > 0 && (int)s->queue.size() >= s->cfg.queue_capacity)
             return CLEORA_ERR_REJECTED;
         j->id = s->next_id++;
         j->res.t_submit = s->now();
-        j->key = j->res.t_submit + service_estimate(*job);
+        j->key = j->res.t_submit + svc;
         s->queue.push_back(j);
         s->jobs[j->id] = j;
         *job_id = j->id;
@@ -340,9 +399,9 @@ int cleora_serve_stats(const cleora_server* s, int* queued, int* running, int64_
     std::lock_guard<std::mutex> lk(m->mu);
     if (queued) *queued = (int)s->queue.size();
     if (running) *running = s->running;
-    if (bytes_reserved) *bytes_reserved = s->reserved;
+    if (bytes_reserved) *bytes_reserved = s->reserved + s->reserved_short;
     if (completed) *completed = s->completed;
-    if (budget) *budget = s->budget;
+    if (budget) *budget = s->budget + s->short_budget;
     return CLEORA_OK;
 }
 
@@ -362,7 +421,12 @@ void cleora_serve_destroy(cleora_server* s) {
     s->cv_work.notify_all();
     s->cv_done.notify_all();
     for (std::thread& t : s->workers) t.join();  // running jobs finish first
-    for (cleora_ctx* c : s->slots) cleora_destroy(c);
+    for (size_t k = 0; k < s->slots.size(); ++k) {
+        s->slots[k]->stream = s->lo[k];  // the slot's own stream; the context owns neither
+        cleora_destroy(s->slots[k]);
+    }
+    for (cudaStream_t x : s->hi) cudaStreamDestroy(x);
+    for (cudaStream_t x : s->lo) cudaStreamDestroy(x);
     delete s;
 }
 

@@ -90,3 +90,17 @@ def test_serving_memory_estimate_model():
     small_t = est(E=E, nodes_hint=100_000, storage="bf16")
     big_t = est(E=E, nodes_hint=2_000_000, storage="bf16")
     assert big_t - small_t > m * 4
+
+
+def test_server_config_is_checked_before_any_cuda_call():
+    """Out-of-range short-slot, short-job and quantum settings are refused on the host."""
+    lib = pkg.cleora.load()
+    for kw in ({"short_slots": -1}, {"short_slots": 65}, {"short_job_seconds": -1.0},
+               {"short_job_seconds": float("nan")}, {"task_quantum": -2}, {"task_quantum": (1 << 20) + 1},
+               {"max_slots": -1}):
+        cfg = pkg.cleora.cleora_server_config(0, 0, 2, 0, 0, 0, 0.0, 0)
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        assert lib.cleora_serve_create(ctypes.byref(h), ctypes.byref(cfg)) == pkg.CLEORA_ERR_INVALID_ARG
+        assert not h.value

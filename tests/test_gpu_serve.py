@@ -179,3 +179,47 @@ def test_next_returns_every_job_once_in_completion_order(jobs):
             assert r[1].status == 0
         assert sorted(seen) == sorted(ids)
         assert srv.next(0) is None  # nothing left
+
+
+def test_short_slots_run_short_jobs_while_long_ones_hold_every_slot(jobs):
+    import time
+    import paper_2102_02302_gb300 as pkg
+    # two long jobs hold both general slots; short jobs that arrive after them run on the short
+    # slot (high-priority stream, long jobs' CTAs retiring after one task per warp) and finish
+    # first, with the same bits as alone
+    longs = [synth.chung_lu_undirected(2_000_000, 20_000_000, 2.1, 30 + k, 200_000.0) for k in range(2)]
+    short = [jobs[k] for k in (0, 4, 7, 9)]
+    alone = [_alone(j) for j in short]
+    with pkg.Server(0, max_slots=2, short_slots=1, short_job_seconds=0.02) as srv:
+        lid = [srv.submit(e.src, e.dst, None, False, 1024, 5, 0, "f32", None) for e in longs]
+        t_end = time.time() + 60
+        while srv.stats()["running"] < 2 and time.time() < t_end:
+            time.sleep(0.001)
+        outs = [np.full(a.shape, np.nan, np.float32) for a in alone]
+        sid = [_submit(srv, j, o) for j, o in zip(short, outs)]
+        res_short = [srv.poll(i, 120_000) for i in sid]
+        res_long = [srv.poll(i, 300_000) for i in lid]
+    assert all(r.status == 0 for r in res_long + res_short)
+    assert all(r.slot == 2 for r in res_short)  # the short slot (slots 0, 1 are general)
+    assert max(r.t_done for r in res_short) < min(r.t_done for r in res_long)
+    for o, a in zip(outs, alone):
+        assert np.array_equal(o, a)
+
+
+def test_persistent_and_quantum_servers_agree(jobs):
+    import paper_2102_02302_gb300 as pkg
+    res = []
+    for q in (-1, 0, 2):
+        outs = []
+        with pkg.Server(0, max_slots=3, short_slots=1, task_quantum=q) as srv:
+            ids = []
+            for j in jobs:
+                e = j["edges"]
+                n = len(np.unique(np.concatenate([e.src, e.dst])))
+                outs.append(np.full((n, j["d"]), np.nan, np.float32))
+                ids.append(_submit(srv, j, outs[-1]))
+            assert all(srv.poll(i, 120_000).status == 0 for i in ids)
+        res.append(outs)
+    for a, b, c in zip(*res):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
