@@ -191,7 +191,8 @@ def test_short_slots_run_short_jobs_while_long_ones_hold_every_slot(jobs):
     short = [jobs[k] for k in (0, 4, 7, 9)]
     alone = [_alone(j) for j in short]
     with pkg.Server(0, max_slots=2, short_slots=1, short_job_seconds=0.02) as srv:
-        lid = [srv.submit(e.src, e.dst, None, False, 1024, 5, 0, "f32", None) for e in longs]
+        lid = [srv.submit(e.src, e.dst, None, False, 1024, 5, 0, "f32", None, nodes_hint=2_000_000)
+               for e in longs]
         t_end = time.time() + 60
         while srv.stats()["running"] < 2 and time.time() < t_end:
             time.sleep(0.001)
