@@ -638,6 +638,10 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
     lat = np.array([r.t_done - a for r, a in zip(results, arr)])[warm:]
     wait = np.array([r.t_admit - a for r, a in zip(results, arr)])[warm:]
     svc = np.array([r.t_done - r.t_admit for r in results])[warm:]
+    # the feeder's wait for output space (arrival -> submit) and the server's own latency
+    # (submit -> result in host memory)
+    feed = np.array([r.t_submit - a for r, a in zip(results, arr)])[warm:]
+    srv_lat = np.array([r.t_done - r.t_submit for r in results])[warm:]
     span = max(r.t_done for r in results[warm:]) - arr[warm]
     work = sum(r.nnz * j[1] * j[2] for r, j in zip(results[warm:], jobs[warm:]))
     big = np.array([pool[j[0]]["n"] * j[1] for j in jobs])[warm:]
@@ -654,6 +658,8 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
                             "p50_ms": float(np.percentile(sel, 50) * 1e3),
                             "p99_ms": float(np.percentile(sel, 99) * 1e3),
                             "queue_wait_p99_ms": float(np.percentile(wait[cls == c], 99) * 1e3),
+                            "feeder_wait_p99_ms": float(np.percentile(feed[cls == c], 99) * 1e3),
+                            "server_latency_p99_ms": float(np.percentile(srv_lat[cls == c], 99) * 1e3),
                             "service_p50_ms": float(np.percentile(svc[cls == c], 50) * 1e3),
                             "service_p99_ms": float(np.percentile(svc[cls == c], 99) * 1e3)})
     return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "short_slots": short_slots,
@@ -663,6 +669,9 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "queue_wait_p50_ms": float(np.percentile(wait, 50) * 1e3),
             "queue_wait_p99_ms": float(np.percentile(wait, 99) * 1e3),
+            "feeder_wait_p99_ms": float(np.percentile(feed, 99) * 1e3),
+            "server_latency_p50_ms": float(np.percentile(srv_lat, 50) * 1e3),
+            "server_latency_p99_ms": float(np.percentile(srv_lat, 99) * 1e3),
             "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
             "service_p99_ms": float(np.percentile(svc, 99) * 1e3),
             "by_size": by_size,
