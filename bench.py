@@ -611,14 +611,13 @@ def serve_run(srv, pool, arena, jobs, arrivals, start):
 
 
 def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0,
-                  arena_bytes=96 << 30, short_slots=2, short_job_s=0.02, task_quantum=0):
+                  arena_bytes=96 << 30, short_slots=2, short_job_s=0.02):
     import paper_2102_02302_gb300 as pkg
     t = time.perf_counter()
     pool = serve_pool(seed=seed)
     arena = PinnedArena(arena_bytes)
     gen_s = time.perf_counter() - t
-    with pkg.Server(device, max_slots=slots, short_slots=short_slots, short_job_seconds=short_job_s,
-                    task_quantum=task_quantum) as srv:
+    with pkg.Server(device, max_slots=slots, short_slots=short_slots, short_job_seconds=short_job_s) as srv:
         # capacity: closed loop (every job available at once; output space is the only gate)
         cap_jobs = serve_jobs(pool, n_capacity, seed + 1)
         t0 = srv.now()
@@ -663,7 +662,7 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
                             "service_p50_ms": float(np.percentile(svc[cls == c], 50) * 1e3),
                             "service_p99_ms": float(np.percentile(svc[cls == c], 99) * 1e3)})
     return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "short_slots": short_slots,
-            "short_job_s": short_job_s, "task_quantum": 1 if task_quantum == 0 else max(0, task_quantum),
+            "short_job_s": short_job_s,
             "failed": n_jobs - len(ok),
             "capacity_jobs_per_s": capacity, "lambda_jobs_per_s": lam,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
@@ -799,8 +798,6 @@ def main():
                     help="skip the 10k-node and 2M-node workloads (GPU and full oracle runs)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-short-slots", type=int, default=2, help="serving slots for short jobs only")
-    ap.add_argument("--serve-quantum", type=int, default=0,
-                    help="tasks per warp before a propagate CTA retires (0: 1, -1: persistent)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-autotune", type=int, default=1, help="1: autotuned schedules, 0: defaults")
     args = ap.parse_args()
@@ -810,8 +807,7 @@ def main():
         import torch
         rank, local_rank, world = env_rank()
         torch.cuda.set_device(local_rank)
-        r = serve_measure(local_rank, args.serve_jobs, short_slots=args.serve_short_slots,
-                          task_quantum=args.serve_quantum)
+        r = serve_measure(local_rank, args.serve_jobs, short_slots=args.serve_short_slots)
         if rank == 0:
             print(json.dumps({"metric": "job p50/p99 latency", "value": r["p99_ms"], "unit": "ms",
                               "n_gpus": world, "steps": args.serve_jobs, "warmup": r["warmup_jobs"],
@@ -939,8 +935,7 @@ def main():
 
     serving = None
     if not args.no_serve:
-        serving = serve_measure(device, args.serve_jobs, short_slots=args.serve_short_slots,
-                                task_quantum=args.serve_quantum)
+        serving = serve_measure(device, args.serve_jobs, short_slots=args.serve_short_slots)
 
     configs = None
     if not args.no_configs and rank == 0 and world == 1:

@@ -168,16 +168,9 @@ typedef enum {
                                     returns CLEORA_ERR_DEVICE), waits again (bounded) and
                                     returns, leaving the context usable.  The results of
                                     that launch are not valid                              */
-    CLEORA_OPT_CHUNK_BYTES = 10, /* device bytes one chunk of cleora_chunked_embed may use
+    CLEORA_OPT_CHUNK_BYTES = 10  /* device bytes one chunk of cleora_chunked_embed may use
                                     when the library picks the chunks; 0 = 80% of the free
                                     device memory at the call                              */
-    CLEORA_OPT_TASK_QUANTUM = 11 /* tasks a warp of the propagate kernel takes before it
-                                    exits (0..2^20); 0 = a persistent grid whose warps run
-                                    until the task queue is empty.  With a quantum the grid
-                                    has one CTA per 8 x quantum tasks, so CTAs retire during
-                                    the launch and kernels on other (higher-priority)
-                                    streams get SMs in between.  Results are the same bits
-                                    for any value (tasks and their sums do not change)     */
 } cleora_option;
 int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value);
 int cleora_get_option(const cleora_ctx* ctx, cleora_option opt, int64_t* value);
@@ -345,9 +338,6 @@ typedef struct {
     double short_job_seconds;  /* a job is short when its estimated service time is at most
                                   this; short jobs run on a high-priority stream in any
                                   slot; 0: 0.02 s                                          */
-    int task_quantum;          /* CLEORA_OPT_TASK_QUANTUM of the slots' contexts: 0 = 1 (a
-                                  long job's propagate CTAs retire after one task per warp,
-                                  so short jobs' kernels get SMs); -1 = persistent grids    */
 } cleora_server_config;
 
 typedef struct {

@@ -36,7 +36,7 @@ DTYPES = {"f32": CLEORA_F32, "float32": CLEORA_F32, "bf16": CLEORA_BF16, "bfloat
 
 OPTIONS = {"vec_bytes": 0, "row_mode": 1, "split_len": 2, "task_nnz": 3, "blocks_per_sm": 4,
            "hot_bytes": 5, "id_slots": 6, "staging": 7, "ring_stages": 8,
-           "test_ring_wait": 9, "chunk_bytes": 10, "task_quantum": 11}
+           "test_ring_wait": 9, "chunk_bytes": 10}
 
 # Every symbol include/cleora.h declares: name -> (restype, argtypes)
 SIGNATURES = {
@@ -557,8 +557,7 @@ class Batch:
 class cleora_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", _I64), ("max_slots", ctypes.c_int),
                 ("queue_capacity", ctypes.c_int), ("inject_alloc_failure_every", ctypes.c_int),
-                ("short_slots", ctypes.c_int), ("short_job_seconds", ctypes.c_double),
-                ("task_quantum", ctypes.c_int)]
+                ("short_slots", ctypes.c_int), ("short_job_seconds", ctypes.c_double)]
 
 
 class cleora_job(ctypes.Structure):
@@ -587,11 +586,10 @@ def _job_struct(src, dst, weights, directed, d, iters, seed, storage, out, nodes
 
 def cleora_serve_create(device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
                         queue_capacity: int = 0, inject_alloc_failure_every: int = 0,
-                        short_slots: int = 0, short_job_seconds: float = 0.0, task_quantum: int = 0):
+                        short_slots: int = 0, short_job_seconds: float = 0.0):
     lib = load()
     cfg = cleora_server_config(device, hbm_budget_bytes, max_slots, queue_capacity,
-                               inject_alloc_failure_every, short_slots, float(short_job_seconds),
-                               task_quantum)
+                               inject_alloc_failure_every, short_slots, float(short_job_seconds))
     h = _P()
     st = lib.cleora_serve_create(ctypes.byref(h), ctypes.byref(cfg))
     if st != CLEORA_OK:
@@ -662,10 +660,10 @@ class Server:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_slots: int = 0,
                  queue_capacity: int = 0, inject_alloc_failure_every: int = 0,
-                 short_slots: int = 0, short_job_seconds: float = 0.0, task_quantum: int = 0):
+                 short_slots: int = 0, short_job_seconds: float = 0.0):
         self.handle = cleora_serve_create(device, hbm_budget_bytes, max_slots, queue_capacity,
                                           inject_alloc_failure_every, short_slots,
-                                          short_job_seconds, task_quantum)
+                                          short_job_seconds)
         self._held = {}  # job id -> arrays the job reads or writes (kept alive until collected)
 
     def submit(self, src, dst, weights=None, directed=False, d=128, iters=4, seed=0,

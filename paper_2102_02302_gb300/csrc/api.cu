@@ -491,9 +491,6 @@ int cleora_set_option(cleora_ctx* ctx, cleora_option opt, int64_t value) {
         case CLEORA_OPT_CHUNK_BYTES:
             if (value < 0) return fail(ctx, CLEORA_ERR_INVALID_ARG, "chunk bytes");
             break;
-        case CLEORA_OPT_TASK_QUANTUM:
-            if (value < 0 || value > ((int64_t)1 << 20)) return fail(ctx, CLEORA_ERR_INVALID_ARG, "task quantum");
-            break;
         case CLEORA_OPT_TEST_RING_WAIT:
             if (value != 0 && value != 1) return fail(ctx, CLEORA_ERR_INVALID_ARG, "test hook");
             break;

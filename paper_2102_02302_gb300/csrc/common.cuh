@@ -65,7 +65,7 @@ struct Shape {
     int chunks = 0; // vectors per row
 };
 
-enum { OPT_COUNT = 12 };
+enum { OPT_COUNT = 11 };
 
 constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
 constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
@@ -91,7 +91,7 @@ struct cleora_ctx {
     int cur = 0;
     int iteration = 0;
 
-    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t opt[cleora::OPT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     CUtensorMap tmap[2];            // ring with 4-row tensor gathers: maps over T[0], T[1]
     bool tmap_ready = false;
     int chunks_used = 0;            // cleora_chunked_embed: chunks of the last call

@@ -690,7 +690,6 @@ int propagate_step(cleora_ctx* ctx, const void* Tin, void* Tout) {
     a.partials = p.partials;
     a.err = ctx->err_flag;
     a.hot_cnt = g.hot_cnt;
-    a.quantum = (int)ctx->opt[CLEORA_OPT_TASK_QUANTUM];
     CL_CUDA(ctx, cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), ctx->stream));
     const int bps = (int)ctx->opt[CLEORA_OPT_BLOCKS_PER_SM];
     cudaError_t e;

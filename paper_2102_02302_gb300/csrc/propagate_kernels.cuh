@@ -20,8 +20,6 @@
 //    neighbour rows and normalises.
 #pragma once
 
-#include <algorithm>
-#include <climits>
 #include <type_traits>
 
 #include "common.cuh"
@@ -75,10 +73,6 @@ struct Args {
     // the rows kept in L2, for the shared-memory ring kernel (rows keep ascending order).
     const uint32_t* hot_bits = nullptr;
     int test_wait_runout = 0;  // ring kernel test hook (see CLEORA_OPT_TEST_RING_WAIT)
-    // Tasks a warp takes before it exits; 0: until the queue is empty (a persistent grid).
-    // With a quantum the grid has one CTA per 8 * quantum tasks, so CTAs retire while the
-    // launch runs and kernels of other streams (by priority) get SMs in between.
-    int quantum = 0;
 };
 
 // L2 policy of a gather: in a partitioned row the hot segment is loaded evict_last and the
@@ -680,8 +674,7 @@ k_propagate(Args a) {
     using K = Kern<ST, VEC, CPL, G, HV, false, 0, FR>;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, lg = lane % G;
-    // (a warp's task count cannot reach INT_MAX: the task table holds fewer tasks)
-    for (int left = a.quantum > 0 ? a.quantum : INT_MAX;; ) {
+    for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1ull);
         t = __shfl_sync(FULL, t, 0);
@@ -695,7 +688,6 @@ k_propagate(Args a) {
             K::rows_group(a, task.a, task.b, g, lg);
         }
         __syncwarp();
-        if (--left == 0) break;
     }
 }
 
@@ -711,13 +703,9 @@ struct Launch {
             if (e != cudaSuccess) return e;
             if (bps < 1) bps = 1;
         }
-        int64_t grid = (int64_t)bps * num_sms;
-        // with a quantum every task needs a warp slot: 8 warps x quantum tasks per CTA (a warp
-        // stops early only when the queue is empty, so these CTAs take every task)
-        if (a.quantum > 0) grid = std::max<int64_t>(1, (a.ntasks + 8ll * a.quantum - 1) / (8ll * a.quantum));
-        if (grid > INT_MAX) return cudaErrorInvalidConfiguration;
-        if (grid_out) *grid_out = (int)grid;
-        kern<<<(unsigned)grid, 256, 0, s>>>(a);
+        int grid = bps * num_sms;
+        if (grid_out) *grid_out = grid;
+        kern<<<grid, 256, 0, s>>>(a);
         return cudaGetLastError();
     }
 

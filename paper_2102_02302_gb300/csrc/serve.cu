@@ -10,9 +10,7 @@
 //
 // Short jobs (estimated service at most short_job_seconds) also have short_slots slots of
 // their own, with a memory reserve of their own, so they never wait for a long job to leave a
-// slot; and every short job runs on a high-priority stream.  Propagate launches retire their
-// CTAs after a quantum of tasks, so a short job's kernels get SMs within about one task of a
-// long job's, instead of after the whole launch.
+// slot; and every short job runs on a high-priority stream.
 //
 // A job runs the whole method on a stream of its slot (upload and build, init, iterations,
 // FP32 result to host), so jobs on different slots overlap on the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver down
@@ -242,8 +240,7 @@ int64_t cleora_serve_estimate(const cleora_job* j) {
 
 int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
     if (!out || !cfg || cfg->max_slots < 0 || cfg->queue_capacity < 0 || cfg->hbm_budget_bytes < 0 ||
-        cfg->short_slots < 0 || cfg->short_slots > 64 || !(cfg->short_job_seconds >= 0.0) ||
-        cfg->task_quantum < -1 || cfg->task_quantum > (1 << 20))
+        cfg->short_slots < 0 || cfg->short_slots > 64 || !(cfg->short_job_seconds >= 0.0))
         return CLEORA_ERR_INVALID_ARG;
     *out = nullptr;
     cleora_server* s = new (std::nothrow) cleora_server();
@@ -252,7 +249,6 @@ int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
     if (s->cfg.max_slots == 0) s->cfg.max_slots = 4;
     if (s->cfg.short_job_seconds > 0.0) s->short_s = s->cfg.short_job_seconds;
     const int all_slots = s->cfg.max_slots + s->cfg.short_slots;
-    const int quantum = s->cfg.task_quantum == 0 ? 1 : std::max(0, s->cfg.task_quantum);
     s->t0 = std::chrono::steady_clock::now();
     {
         DeviceGuard guard(cfg->device);
@@ -291,10 +287,7 @@ int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
         s->lo.push_back(l);
         cleora_ctx* c = nullptr;
         rc = cleora_create(&c, cfg->device, l);
-        if (rc == CLEORA_OK) {
-            s->slots.push_back(c);
-            rc = cleora_set_option(c, CLEORA_OPT_TASK_QUANTUM, quantum);
-        }
+        if (rc == CLEORA_OK) s->slots.push_back(c);
     }
     if (rc != CLEORA_OK) {
         for (cleora_ctx* x : s->slots) cleora_destroy(x);

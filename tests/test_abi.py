@@ -93,12 +93,11 @@ def test_serving_memory_estimate_model():
 
 
 def test_server_config_is_checked_before_any_cuda_call():
-    """Out-of-range short-slot, short-job and quantum settings are refused on the host."""
+    """Out-of-range slot counts and short-job limits are refused on the host."""
     lib = pkg.cleora.load()
     for kw in ({"short_slots": -1}, {"short_slots": 65}, {"short_job_seconds": -1.0},
-               {"short_job_seconds": float("nan")}, {"task_quantum": -2}, {"task_quantum": (1 << 20) + 1},
-               {"max_slots": -1}):
-        cfg = pkg.cleora.cleora_server_config(0, 0, 2, 0, 0, 0, 0.0, 0)
+               {"short_job_seconds": float("nan")}, {"max_slots": -1}, {"queue_capacity": -1}):
+        cfg = pkg.cleora.cleora_server_config(0, 0, 2, 0, 0, 0, 0.0)
         for k, v in kw.items():
             setattr(cfg, k, v)
         h = ctypes.c_void_p()

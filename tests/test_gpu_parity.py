@@ -153,7 +153,6 @@ SCHEDULES = {
     "row_groups": {"row_mode": 2},
     "row_groups_vec8_split": {"row_mode": 2, "vec_bytes": 8, "split_len": 300, "task_nnz": 100},
     "one_block": {"blocks_per_sm": 1, "task_nnz": 1024},
-    "quantum_split": {"task_quantum": 1, "split_len": 256, "task_nnz": 64},
 }
 
 
@@ -177,19 +176,6 @@ def test_f32_schedules_and_dims(sched, d, graphs, oracle_graphs):
     want = oracle.propagate(g, oracle.init(g.ids, d, 3), 3)
     _, got = gpu_run(e, d, 3, seed=3, opts=SCHEDULES[sched])
     assert_close_f32(got, want)
-
-
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
-@pytest.mark.parametrize("d", [64, 256])
-def test_task_quantum_gives_the_same_bits(storage, d, graphs):
-    # warps that exit after a quantum of tasks take the same tasks with the same sums; split
-    # rows are combined by whichever chunk arrives last, in chunk order
-    e = graphs["star_hub"]
-    base = {"split_len": 256, "task_nnz": 64}
-    _, want = gpu_run(e, d, 3, seed=5, storage=storage, opts=base)
-    for q in (1, 3, 1 << 20):
-        _, got = gpu_run(e, d, 3, seed=5, storage=storage, opts=dict(base, task_quantum=q))
-        assert np.array_equal(got, want)
 
 
 @pytest.mark.parametrize("sched", list(SCHEDULES))
