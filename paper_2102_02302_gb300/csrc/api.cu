@@ -76,7 +76,7 @@ int copy_out(cleora_ctx* ctx, void* out, const void* dev, size_t bytes, int out_
 
 int check_err_flag(cleora_ctx* ctx) {
     int flag = 0;
-    CL_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CL_CUDA(ctx, read_back(ctx, &flag, ctx->err_flag, sizeof(int), ctx->stream));
     CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (flag) {
         CL_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->stream));
@@ -165,6 +165,46 @@ int import_T(cleora_ctx* ctx, const void* in, cleora_dtype dtype, int in_on_devi
 
 }  // namespace
 
+namespace {
+struct Bytes32 {
+    unsigned char b[32];
+};
+__global__ void k_put_bytes(unsigned char* dst, Bytes32 v, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = v.b[i];
+}
+}  // namespace
+
+cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s) {
+    unsigned char* h = static_cast<unsigned char*>(host);
+    const unsigned char* d = static_cast<const unsigned char*>(dev);
+    if (!ctx->host_stage) {  // (contexts always have one; kept for safety)
+        cudaError_t e = cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+        return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+    }
+    do {
+        const size_t c = std::min(bytes, HOST_STAGE_BYTES);
+        cudaError_t e = cudaMemcpyAsync(ctx->host_stage, d, c, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        memcpy(h, ctx->host_stage, c);
+        h += c;
+        d += c;
+        bytes -= c;
+    } while (bytes > 0);
+    return cudaSuccess;
+}
+
+cudaError_t put_bytes(cleora_ctx* ctx, void* dev, const void* host, size_t bytes, cudaStream_t s) {
+    if (bytes > sizeof(Bytes32)) return cudaErrorInvalidValue;
+    if (bytes == 0) return cudaSuccess;
+    Bytes32 v;
+    memcpy(v.b, host, bytes);
+    k_put_bytes<<<1, 32, 0, s>>>(static_cast<unsigned char*>(dev), v, (int)bytes);
+    ctx->launches += 1;
+    return cudaGetLastError();
+}
+
+
 void ctx_release_all(cleora_ctx* ctx) {
     plan_release(ctx);
     embeddings_release(ctx);
@@ -227,6 +267,12 @@ int cleora_create(cleora_ctx** out, int device, void* cuda_stream) {
         uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse until destroy
         cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         if ((rc = dalloc(ctx, &ctx->err_flag, 1)) != CLEORA_OK) break;
+        e = cudaHostAlloc((void**)&ctx->host_stage, HOST_STAGE_BYTES, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            ctx->host_stage = nullptr;
+            rc = CLEORA_ERR_OOM;
+            break;
+        }
         e = cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) { rc = CLEORA_ERR_CUDA; break; }
@@ -253,6 +299,7 @@ void cleora_destroy(cleora_ctx* ctx) {
             if (ctx->stream) cudaStreamSynchronize(ctx->stream);
             cudaMemPoolDestroy(ctx->pool);
         }
+        if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
         cudaGetLastError();
     }
@@ -353,7 +400,7 @@ int cleora_get_csr(cleora_ctx* ctx, int64_t* rowptr, int32_t* col, float* val, f
     if (g.n == 0) {
         if (rowptr) {
             int64_t z = 0;
-            if (out_on_device) CL_CUDA(ctx, cudaMemcpyAsync(rowptr, &z, 8, cudaMemcpyHostToDevice, ctx->stream));
+            if (out_on_device) CL_CUDA(ctx, put_bytes(ctx, rowptr, &z, 8, ctx->stream));
             else *rowptr = 0;
             CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         }

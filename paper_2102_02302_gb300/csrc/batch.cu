@@ -731,7 +731,7 @@ int cleora_batch_run(cleora_batch* b, float* out, int out_on_device) {
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return from_ctx(b, cuda_fail(c, e, "batch run", __FILE__, __LINE__));
     int flag = 0;
-    e = cudaMemcpy(&flag, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    e = read_back(c, &flag, c->err_flag, sizeof(int), c->stream);
     if (e == cudaSuccess && flag) {
         cudaMemset(c->err_flag, 0, sizeof(int));
         return bfail(b, CLEORA_ERR_DEVICE, "a kernel reported an inconsistency (flag %d)", flag);

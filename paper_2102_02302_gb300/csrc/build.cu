@@ -494,7 +494,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         k_check_weights<<<grid_for(E, 256, sms), 256, 0, s>>>(w, E, d_flag);
         CL_LAUNCHED(ctx);
         int bad = 0;
-        CL_CUDA(ctx, cudaMemcpyAsync(&bad, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, read_back(ctx, &bad, d_flag, sizeof(int), s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
         if (bad) return fail(ctx, CLEORA_ERR_INVALID_ARG, "weights must be finite and > 0");
     }
@@ -525,7 +525,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
             k_hll<<<grid_for(2 * E, 256, sms), 256, 0, s>>>(src, dst, E, regs.p);
             CL_LAUNCHED(ctx);
             std::vector<unsigned int> hr(HLL_M);
-            CL_CUDA(ctx, cudaMemcpyAsync(hr.data(), regs.p, HLL_M * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+            CL_CUDA(ctx, read_back(ctx, hr.data(), regs.p, HLL_M * sizeof(unsigned int), s));
             CL_CUDA(ctx, cudaStreamSynchronize(s));
             const double est = hll_estimate(hr.data());
             uint64_t want = 1 << 16;
@@ -540,7 +540,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
                                                                     d_flag, d_overflow);
             CL_LAUNCHED(ctx);
             int ovf = 0;
-            CL_CUDA(ctx, cudaMemcpyAsync(&ovf, d_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CL_CUDA(ctx, read_back(ctx, &ovf, d_overflow, sizeof(int), s));
             CL_CUDA(ctx, cudaStreamSynchronize(s));
             if (!ovf) break;
             if (S == S_full) return fail(ctx, CLEORA_ERR_DEVICE, "id set overflow");
@@ -557,7 +557,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         // in-place compaction keeps the selected ids in order at the front of the table
         CL_CUDA(ctx, cub::DeviceSelect::If(tmp.p, tb, kk.p, scal.p, (int64_t)S, pred, s));
         int64_t hv[2] = {0, 0};
-        CL_CUDA(ctx, cudaMemcpyAsync(hv, scal.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, read_back(ctx, hv, scal.p, 2 * sizeof(int64_t), s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
         has_empty = (int)(hv[1] & 0xffffffff);
         const int64_t n = hv[0] + (has_empty ? 1 : 0);
@@ -582,7 +582,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
         }
         if (has_empty) {
             const uint64_t e = EMPTY_ID;
-            CL_CUDA(ctx, cudaMemcpyAsync(g.ids + hv[0], &e, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+            CL_CUDA(ctx, put_bytes(ctx, g.ids + hv[0], &e, sizeof(uint64_t), s));
         }
         // id -> rank table, at least twice as many slots as ids
         uint64_t slots = 2;
@@ -615,7 +615,7 @@ int graph_build_impl(cleora_ctx* ctx, const uint64_t* src, const uint64_t* dst, 
                                                        has_empty, bits, invalid, ka, w ? va.p : nullptr, d_flag);
         CL_LAUNCHED(ctx);
         int missing = 0;
-        CL_CUDA(ctx, cudaMemcpyAsync(&missing, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, read_back(ctx, &missing, d_flag, sizeof(int), s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
         if (missing) return fail(ctx, CLEORA_ERR_DEVICE, "endpoint missing from the id table");
     }
@@ -681,7 +681,7 @@ int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float*
         CL_CUDA(ctx, cub::DeviceSelect::Flagged(tmp.p, tb, it, head, start, scal.p, m, s));
     }
     int64_t nnz = 0;
-    CL_CUDA(ctx, cudaMemcpyAsync(&nnz, scal.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, read_back(ctx, &nnz, scal.p, sizeof(int64_t), s));
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     g.nnz = nnz;
 
@@ -709,7 +709,7 @@ int csr_from_entries(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float*
     CL_LAUNCHED(ctx);
 
     int64_t hv[3] = {0, 0, 0};
-    CL_CUDA(ctx, cudaMemcpyAsync(hv, scal.p, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, read_back(ctx, hv, scal.p, 3 * sizeof(int64_t), s));
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     const int not_unit = (int)(hv[1] & 0xffffffff);
     g.max_row_len = hv[2];
@@ -778,9 +778,9 @@ int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* v
         CL_TRY(tmp.alloc(tb));
         CL_CUDA(ctx, cub::DeviceSelect::Flagged(tmp.p, tb, it, head, start, scal.p, E, s));
     }
-    CL_CUDA(ctx, cudaMemcpyAsync(scal.p + 3, &m_valid, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CL_CUDA(ctx, put_bytes(ctx, scal.p + 3, &m_valid, sizeof(int64_t), s));
     int64_t nu = 0;
-    CL_CUDA(ctx, cudaMemcpyAsync(&nu, scal.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, read_back(ctx, &nu, scal.p, sizeof(int64_t), s));
     CL_CUDA(ctx, cudaStreamSynchronize(s));
 
     // 3. per pair: lo, hi, e (FP64 weight sum in edge order; unweighted: the multiplicity)
@@ -793,7 +793,7 @@ int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* v
                                                   weighted ? pe.p : nullptr, d_flag);
     CL_LAUNCHED(ctx);
     int flag = 0;
-    CL_CUDA(ctx, cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, read_back(ctx, &flag, d_flag, sizeof(int), s));
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     const bool not_unit = flag != 0;
     const bool has_val = weighted || not_unit;
@@ -823,7 +823,7 @@ int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* v
     }
     k_count_below<<<1, 1, 0, s>>>(tk, nu, (uint32_t)n, scal.p);
     CL_LAUNCHED(ctx);
-    CL_CUDA(ctx, cudaMemcpyAsync(&nt, scal.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, read_back(ctx, &nt, scal.p, sizeof(int64_t), s));
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     const int64_t nnz = nu + nt;
     g.nnz = nnz;
@@ -863,7 +863,7 @@ int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* v
         k_degree_len<<<grid_for(n, 256, sms), 256, 0, s>>>(g.rowptr, n, g.deg, g.inv_deg, d_max);
     CL_LAUNCHED(ctx);
     int64_t max_len = 0;
-    CL_CUDA(ctx, cudaMemcpyAsync(&max_len, scal.p + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CL_CUDA(ctx, read_back(ctx, &max_len, scal.p + 2, sizeof(int64_t), s));
     CL_CUDA(ctx, cudaStreamSynchronize(s));
     g.max_row_len = max_len;
     g.has_val = has_val;
@@ -920,7 +920,7 @@ int sort_unique_ids(cleora_ctx* ctx, const uint64_t* keys, int64_t count, uint64
         CL_CUDA(ctx, cub::DeviceRadixSort::SortKeys(tmp.p, tb, db, count, 0, 64, s));
         CL_CUDA(ctx, cub::DeviceSelect::Unique(tmp.p, tu, db.Current(), db.Alternate(), num.p, count, s));
         int64_t n = 0;
-        CL_CUDA(ctx, cudaMemcpyAsync(&n, num.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, read_back(ctx, &n, num.p, sizeof(int64_t), s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
         CL_TRY(dalloc(ctx, ids_out, (size_t)(n ? n : 1)));
         CL_CUDA(ctx, cudaMemcpyAsync(*ids_out, db.Alternate(), n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
@@ -939,7 +939,7 @@ int check_weights(cleora_ctx* ctx, const float* w, int64_t E) {
     k_check_weights<<<grid_for(E, 256, ctx->num_sms), 256, 0, ctx->stream>>>(w, E, flag.p);
     CL_LAUNCHED(ctx);
     int bad = 0;
-    CL_CUDA(ctx, cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CL_CUDA(ctx, read_back(ctx, &bad, flag.p, sizeof(int), ctx->stream));
     CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (bad) return fail(ctx, CLEORA_ERR_INVALID_ARG, "weights must be finite and > 0");
     return CLEORA_OK;

@@ -70,6 +70,7 @@ enum { OPT_COUNT = 11 };
 constexpr int64_t DEFAULT_SPLIT_LEN = 8192;  // rows longer than this are split across warps
 constexpr int64_t DEFAULT_TASK_NNZ = 4096;   // entries per row-run task
 constexpr int64_t DEFAULT_HOT_BYTES = (int64_t)72 << 20;  // L2 share kept for hot rows
+constexpr size_t HOST_STAGE_BYTES = (size_t)128 << 10;     // pinned staging for small copies
 
 }  // namespace cleora
 
@@ -97,6 +98,7 @@ struct cleora_ctx {
     int chunks_used = 0;            // cleora_chunked_embed: chunks of the last call
     int64_t chunk_peak_bytes = 0;   // ... and the pool's high-water mark during it
     int* err_flag = nullptr;  // device int, raised by kernels
+    unsigned char* host_stage = nullptr;  // pinned, cleora::HOST_STAGE_BYTES: small read-backs
     int64_t launches = 0;
     int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails
 };
@@ -119,6 +121,15 @@ int cuda_fail(cleora_ctx* ctx, cudaError_t e, const char* what, const char* file
         cudaError_t e_ = cudaGetLastError();                                        \
         if (e_ != cudaSuccess) return ::cleora::cuda_fail(ctx, e_, "kernel launch", __FILE__, __LINE__); \
     } while (0)
+
+// Small copies between host and device.  A copy to or from pageable host memory is staged
+// by the driver and waits behind large copies that other streams have in flight: on a GB300 an
+// 8-byte pageable read-back waited up to 90 ms behind a 16 GiB device-to-host copy on another
+// stream, against 0.015 ms through pinned memory or a kernel.  So read-backs go through the
+// context's pinned staging buffer (the copy, then a synchronize of `s`, as a pageable copy
+// would), and small values go to the device as kernel arguments.
+cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s);
+cudaError_t put_bytes(cleora_ctx* ctx, void* dev, const void* host, size_t bytes, cudaStream_t s);  // bytes <= 32
 
 #define CL_TRY(x)                      \
     do {                               \

@@ -223,7 +223,7 @@ int cleora_inductive(cleora_ctx* ctx, const uint64_t* new_ids, const uint64_t* n
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "select", __FILE__, __LINE__); break; }
         }
         int64_t nkept = 0;
-        cudaError_t e = cudaMemcpyAsync(&nkept, scal, 8, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = read_back(ctx, &nkept, scal, 8, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "inductive", __FILE__, __LINE__); break; }
         if (num_dropped) *num_dropped = E - nkept;
@@ -454,7 +454,7 @@ int cleora_chunked_embed(cleora_ctx* ctx, const uint64_t* src, const uint64_t* d
             if (e == cudaSuccess && (rc = cub_tmp(tb))) break;
             if (e == cudaSuccess) e = cub::DeviceRunLengthEncode::Encode(tmp, tb, sorted, spare, cu, scal, m, s);
             int64_t nu = 0;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&nu, scal, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = read_back(ctx, &nu, scal, 8, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "chunk ids", __FILE__, __LINE__); break; }
             ctx->launches += 2;
@@ -491,7 +491,7 @@ int cleora_chunked_embed(cleora_ctx* ctx, const uint64_t* src, const uint64_t* d
             if (e == cudaSuccess)
                 e = cub::DeviceReduce::ReduceByKey(tmp, tb, k2.Current(), V, v2.Current(), occ_all, scal,
                                                    cuda::std::plus<unsigned long long>(), mm, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&nV, scal, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = read_back(ctx, &nV, scal, 8, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "chunk ids", __FILE__, __LINE__); break; }
             ctx->launches += 2;

@@ -163,8 +163,8 @@ int expand(cleora_ctx* ctx, const uint64_t* members, const int64_t* hoff, int64_
     const int sms = ctx->num_sms;
     int64_t M = 0, first = 0;
     if (on_device) {
-        CL_CUDA(ctx, cudaMemcpyAsync(&M, hoff + H, 8, cudaMemcpyDeviceToHost, s));
-        CL_CUDA(ctx, cudaMemcpyAsync(&first, hoff, 8, cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, read_back(ctx, &M, hoff + H, 8, s));
+        CL_CUDA(ctx, read_back(ctx, &first, hoff, 8, s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
     } else {
         M = hoff[H];
@@ -225,7 +225,7 @@ int expand(cleora_ctx* ctx, const uint64_t* members, const int64_t* hoff, int64_
             e = cub::DeviceSelect::Flagged(nullptr, tb, sorted, flag, U, scal, M, s);
             if (e == cudaSuccess && (rc = cub_tmp(tb))) break;
             if (e == cudaSuccess) e = cub::DeviceSelect::Flagged(tmp, tb, sorted, flag, U, scal, M, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&Mu, scal, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = read_back(ctx, &Mu, scal, 8, s);
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "expansion", __FILE__, __LINE__); break; }
             ctx->launches += 2;
         } else {
@@ -243,10 +243,10 @@ int expand(cleora_ctx* ctx, const uint64_t* members, const int64_t* hoff, int64_
         if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tmp, tb, kd, uoff, H, s);
         int64_t last_e = 0, last_c = 0;
         int64_t last_k = 0, last_u = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&last_e, eoff + H - 1, 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&last_c, cnt + H - 1, 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&last_u, uoff + H - 1, 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&last_k, kd + H - 1, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = read_back(ctx, &last_e, eoff + H - 1, 8, s);
+        if (e == cudaSuccess) e = read_back(ctx, &last_c, cnt + H - 1, 8, s);
+        if (e == cudaSuccess) e = read_back(ctx, &last_u, uoff + H - 1, 8, s);
+        if (e == cudaSuccess) e = read_back(ctx, &last_k, kd + H - 1, 8, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "expansion", __FILE__, __LINE__); break; }
         ctx->launches += 2;
@@ -304,8 +304,8 @@ int cleora_hash_ids(cleora_ctx* ctx, const uint8_t* bytes, const int64_t* offset
     cudaStream_t s = ctx->stream;
     int64_t total = 0, first = 0;
     if (inputs_on_device) {
-        CL_CUDA(ctx, cudaMemcpyAsync(&total, offsets + count, 8, cudaMemcpyDeviceToHost, s));
-        CL_CUDA(ctx, cudaMemcpyAsync(&first, offsets, 8, cudaMemcpyDeviceToHost, s));
+        CL_CUDA(ctx, read_back(ctx, &total, offsets + count, 8, s));
+        CL_CUDA(ctx, read_back(ctx, &first, offsets, 8, s));
         CL_CUDA(ctx, cudaStreamSynchronize(s));
     } else {
         total = offsets[count];

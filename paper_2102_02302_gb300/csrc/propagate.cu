@@ -333,7 +333,7 @@ int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz) {
         e = cub::DeviceSelect::Flagged(tmp, tb, it, brk, rows, scal, g.n, s);
         dfree(ctx, tmp);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "select", __FILE__, __LINE__); break; }
-        e = cudaMemcpyAsync(&nb, scal, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        e = read_back(ctx, &nb, scal, sizeof(int64_t), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "plan count", __FILE__, __LINE__); break; }
         if ((rc = dalloc(ctx, &work, (size_t)(6 * nb)))) break;
@@ -355,7 +355,7 @@ int plan_build(cleora_ctx* ctx, int64_t split_len, int64_t task_nnz) {
         const int64_t* srcs[6] = {cbase + nb - 1, chunks + nb - 1, nbase + nb - 1,
                                   normal + nb - 1, sbase + nb - 1, split + nb - 1};
         for (int k = 0; k < 6 && e == cudaSuccess; ++k)
-            e = cudaMemcpyAsync(&last[k], srcs[k], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            e = read_back(ctx, &last[k], srcs[k], sizeof(int64_t), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "plan totals", __FILE__, __LINE__); break; }
         p.nsplit_chunks = last[0] + last[1];
@@ -544,7 +544,7 @@ int hot_partition(cleora_ctx* ctx) {
         k_bins<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, g.n, bin, hist);
         ctx->launches += 2;
         unsigned long long h[128];
-        e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+        e = read_back(ctx, h, hist, sizeof(h), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
         const int64_t rows = budget / row_bytes;
@@ -558,13 +558,13 @@ int hot_partition(cleora_ctx* ctx) {
         int fb = FINE + 1;  // bucket threshold inside bin b (none)
         if (b >= 1 && h[b] > 0 && acc < rows) {
             const unsigned init[2] = {0xffffffffu, 0u};
-            e = cudaMemcpyAsync(lohi, init, sizeof(init), cudaMemcpyHostToDevice, s);
+            e = put_bytes(ctx, lohi, init, sizeof(init), s);
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
             k_bin_range<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, bin, g.n, b, lohi);
             k_bin_fine<<<grid_for(g.n, 256, sms), 256, 0, s>>>(cnt, bin, g.n, b, lohi, hist + 128);
             ctx->launches += 2;
             std::vector<unsigned long long> f(FINE);
-            e = cudaMemcpyAsync(f.data(), hist + 128, FINE * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+            e = read_back(ctx, f.data(), hist + 128, FINE * sizeof(unsigned long long), s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
             for (int q = FINE - 1; q >= 0; --q) {  // the rows of the top buckets that still fit
@@ -590,9 +590,9 @@ int hot_partition(cleora_ctx* ctx) {
             uint32_t last_word = 0;
             e = cub::DeviceScan::ExclusiveSum(tmp, tb, wcnt, wcnt, nw, s);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(&last_base, wcnt + nw - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+                e = read_back(ctx, &last_base, wcnt + nw - 1, sizeof(int64_t), s);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(&last_word, word + nw - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+                e = read_back(ctx, &last_word, word + nw - 1, sizeof(uint32_t), s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
             ctx->launches++;
@@ -616,7 +616,7 @@ int hot_partition(cleora_ctx* ctx) {
                                                        word, wcnt, nw, rowH, col2, val2);
         ctx->launches += 2;
         int64_t hot_total = 0;
-        e = cudaMemcpyAsync(&hot_total, rowH + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        e = read_back(ctx, &hot_total, rowH + g.n, sizeof(int64_t), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "hot partition", __FILE__, __LINE__); break; }
