@@ -99,12 +99,14 @@ __device__ __forceinline__ void fill_args(prop::Args& a, const BatchArgs& ba, co
 // values): its kernel runs exactly one variant of the single-graph kernel's device code.  A
 // task of another variant (none is ever packed into the family) raises bit 2 of the error
 // flag.
-// CTAs per SM a batch kernel is compiled for: a notch below its single-graph twin, whose
-// arguments sit in the parameter bank, while a batch task's arguments take registers.
+// CTAs per SM a batch kernel is compiled for: its single-graph twin's where whole warps take
+// the rows (4 at 64 registers, no spills), else a notch below it, since a batch task's
+// arguments take registers where the twin's sit in the parameter bank.
 template <typename ST, int VEC, int CPL, int G, bool HV>
 constexpr int batch_min_blocks() {
     constexpr int m = prop::min_blocks<ST, VEC, CPL, G, HV>();
-    return m >= 8 ? 6 : m >= 6 ? 5 : m >= 4 ? 3 : 1;
+    // (whole-warp rows fit 64 registers at 4 CTAs/SM without spills; lane groups need 80)
+    return m >= 8 ? 6 : m >= 6 ? 5 : m >= 4 ? (G == 32 ? 4 : 3) : 1;
 }
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
