@@ -60,10 +60,14 @@ constexpr int variant_of(int G, int mode, bool hv) {
     return (hv ? 16 : 0) | (mode == 2 ? 8 : 0) | (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : G == 16 ? 4 : 5);
 }
 
+// Vectors in flight per lane: the single-graph kernel's (0: prop::inflight), except lane
+// groups of 16-byte gathers, which take 2 so that they fit 4 CTAs/SM.
+template <int VEC, int G>
+constexpr int batch_inflight() { return VEC == 16 && G < 32 ? 2 : 0; }
+
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
 __device__ __forceinline__ void run_task(const prop::Args& a, const Task& t, int lane) {
-    // the single-graph kernel's vectors in flight for this shape (prop::inflight)
-    using K = prop::Kern<ST, VEC, CPL, G, HV>;
+    using K = prop::Kern<ST, VEC, CPL, G, HV, false, batch_inflight<VEC, G>()>;
     const int g = lane / G, lg = lane % G;
     if (t.c >= 0) K::split_chunk(a, t, lane, g, lg);
     else if (MODE == 1 || G == 32) K::rows_coop(a, t.a, t.b, lane, g, lg);
@@ -106,7 +110,7 @@ template <typename ST, int VEC, int CPL, int G, bool HV>
 constexpr int batch_min_blocks() {
     constexpr int m = prop::min_blocks<ST, VEC, CPL, G, HV>();
     // (whole-warp rows fit 64 registers at 4 CTAs/SM without spills; lane groups need 80)
-    return m >= 8 ? 6 : m >= 6 ? 5 : m >= 4 ? (G == 32 ? 4 : 3) : 1;
+    return m >= 8 ? 6 : m >= 6 ? 5 : m >= 4 ? (G == 32 || VEC == 16 ? 4 : 3) : 1;
 }
 
 template <typename ST, int VEC, int CPL, int G, int MODE, bool HV>
