@@ -396,12 +396,14 @@ __global__ void k_counts_to_e(const int64_t* start, int64_t nu, int64_t m_valid,
 }
 
 // Keys of the transposed half: hi, or n for a self-loop (no transposed copy; sorts last).
-__global__ void k_transpose_keys(const int32_t* lo, const int32_t* hi, int64_t nu, uint32_t n, uint32_t* tk,
-                                 uint32_t* tv) {
+// (the sort's value is the pair index when the pairs carry values, else the lower end itself,
+// which the placement then writes without a gather)
+__global__ void k_transpose_keys(const int32_t* lo, const int32_t* hi, int64_t nu, uint32_t n, bool by_pair,
+                                 uint32_t* tk, uint32_t* tv) {
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
          u += (int64_t)gridDim.x * blockDim.x) {
         tk[u] = lo[u] == hi[u] ? n : (uint32_t)hi[u];
-        tv[u] = (uint32_t)u;
+        tv[u] = by_pair ? (uint32_t)u : (uint32_t)lo[u];
     }
 }
 
@@ -421,7 +423,8 @@ __global__ void k_add_rowptr(const int64_t* a, const int64_t* b, int64_t n, int6
         out[r] = a[r] + b[r];
 }
 
-// Lower part of each row: transposed entry i (row tk[i], pair tv[i]) at its rank in the row.
+// Lower part of each row: transposed entry i (row tk[i]; pair tv[i], or with no values its
+// lower end tv[i] itself) at its rank in the row.
 __global__ void k_place_low(const uint32_t* tk, const uint32_t* tv, int64_t nt, const int64_t* rowptr,
                             const int64_t* lowptr, const int32_t* lo, const double* e_u, int32_t* col,
                             double* e_out, int32_t* row_out) {
@@ -429,9 +432,13 @@ __global__ void k_place_low(const uint32_t* tk, const uint32_t* tv, int64_t nt, 
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = tk[i], u = tv[i];
         const int64_t pos = rowptr[r] + (i - lowptr[r]);
-        col[pos] = lo[u];
-        if (e_out) e_out[pos] = e_u[u];
-        if (row_out) row_out[pos] = (int32_t)r;
+        if (e_out) {
+            col[pos] = lo[u];
+            e_out[pos] = e_u[u];
+            row_out[pos] = (int32_t)r;
+        } else {
+            col[pos] = (int32_t)u;
+        }
     }
 }
 
@@ -809,7 +816,7 @@ int csr_undirected(cleora_ctx* ctx, uint64_t* kbuf_a, uint64_t* kbuf_b, float* v
     uint32_t* tk2 = tv + nu;
     uint32_t* tv2 = tk2 + nu;  // 16 nu bytes <= 16 E bytes of kbuf_a
     int64_t nt = 0;
-    k_transpose_keys<<<grid_for(nu, 256, sms), 256, 0, s>>>(plo.p, phi.p, nu, (uint32_t)n, tk, tv);
+    k_transpose_keys<<<grid_for(nu, 256, sms), 256, 0, s>>>(plo.p, phi.p, nu, (uint32_t)n, has_val, tk, tv);
     CL_LAUNCHED(ctx);
     {
         cub::DoubleBuffer<uint32_t> dk(tk, tk2), dv(tv, tv2);
