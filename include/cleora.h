@@ -372,11 +372,11 @@ typedef struct {
  * gathered bytes), so short jobs go ahead of long ones while a job is only passed by jobs
  * that arrived within its own service estimate after it.  A job passed over 8 times because
  * it did not fit stops later jobs from passing it.  A short_slots slot takes the earliest short
- * job that fits its reserve.  Jobs on different slots overlap on the GPU.  After
- * a job, its slot returns the memory it held to the driver (pool trim) except a cache of
- * min(1 GiB, budget / (8 x all slots)) per slot, which is set aside from the budget, so the
- * budget tracks what running jobs and the slot caches hold.  cleora_serve_stats reports the
- * general budget and the short reserve together. */
+ * job that fits its reserve.  Jobs on different slots overlap on the GPU.  The slots allocate
+ * from one device memory pool that keeps what finished jobs freed for the next ones (it is
+ * returned to the driver when an allocation would otherwise fail, and at destroy), so the
+ * budget bounds what running jobs hold.  cleora_serve_stats reports the general budget and
+ * the short reserve together. */
 int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg);
 /* Queues a job; *job_id identifies it.  CLEORA_ERR_REJECTED: its estimate exceeds the whole
  * budget, or the queue is full.  CLEORA_ERR_INVALID_ARG: a malformed job. */

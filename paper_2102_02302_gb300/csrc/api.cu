@@ -33,6 +33,11 @@ int dalloc_bytes(cleora_ctx* ctx, void** p, size_t bytes) {
     if (ctx->inject_alloc_fail >= 0 && ctx->inject_alloc_fail-- == 0)
         return fail(ctx, CLEORA_ERR_OOM, "injected allocation failure (test hook)");
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) {  // the pool keeps freed blocks: hand the unused ones back, try again
+        cudaGetLastError();
+        cudaMemPoolTrimTo(ctx->pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, ctx->pool, ctx->stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -233,6 +238,14 @@ const char* cleora_status_string(int status) {
 }
 
 int cleora_create(cleora_ctx** out, int device, void* cuda_stream) {
+    return ctx_create(out, device, cuda_stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace cleora {
+
+int ctx_create(cleora_ctx** out, int device, void* cuda_stream, cudaMemPool_t shared_pool) {
     if (!out) return CLEORA_ERR_INVALID_ARG;
     *out = nullptr;
     int ndev = 0;
@@ -256,16 +269,21 @@ int cleora_create(cleora_ctx** out, int device, void* cuda_stream) {
             if (e != cudaSuccess) { rc = CLEORA_ERR_CUDA; break; }
             ctx->own_stream = true;
         }
-        cudaMemPoolProps props;
-        memset(&props, 0, sizeof(props));
-        props.allocType = cudaMemAllocationTypePinned;
-        props.handleTypes = cudaMemHandleTypeNone;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = device;
-        e = cudaMemPoolCreate(&ctx->pool, &props);
-        if (e != cudaSuccess) { rc = CLEORA_ERR_CUDA; break; }
-        uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse until destroy
-        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (shared_pool) {
+            ctx->pool = shared_pool;
+            ctx->own_pool = false;
+        } else {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            e = cudaMemPoolCreate(&ctx->pool, &props);
+            if (e != cudaSuccess) { rc = CLEORA_ERR_CUDA; break; }
+            uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse until destroy
+            cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
         if ((rc = dalloc(ctx, &ctx->err_flag, 1)) != CLEORA_OK) break;
         e = cudaHostAlloc((void**)&ctx->host_stage, HOST_STAGE_BYTES, cudaHostAllocDefault);
         if (e != cudaSuccess) {
@@ -286,6 +304,10 @@ int cleora_create(cleora_ctx** out, int device, void* cuda_stream) {
     return CLEORA_OK;
 }
 
+}  // namespace cleora
+
+extern "C" {
+
 void cleora_destroy(cleora_ctx* ctx) {
     if (!ctx) return;
     {
@@ -297,7 +319,7 @@ void cleora_destroy(cleora_ctx* ctx) {
             graph_release(ctx);
             dfree_null(ctx, ctx->err_flag);
             if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-            cudaMemPoolDestroy(ctx->pool);
+            if (ctx->own_pool) cudaMemPoolDestroy(ctx->pool);
         }
         if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

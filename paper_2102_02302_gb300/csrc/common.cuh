@@ -79,6 +79,7 @@ struct cleora_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaMemPool_t pool = nullptr;
+    bool own_pool = true;  // false: a pool shared with other contexts (serving slots)
     int num_sms = 0;
     std::string err;
 
@@ -139,6 +140,9 @@ cudaError_t put_bytes(cleora_ctx* ctx, void* dev, const void* host, size_t bytes
 
 // ---- stream-ordered device memory from the context's pool ----------------------------
 int dalloc_bytes(cleora_ctx* ctx, void** p, size_t bytes);
+// A context on `device`; with `shared_pool` its allocations come from that pool, which the
+// caller owns and destroys after the context.
+int ctx_create(cleora_ctx** out, int device, void* cuda_stream, cudaMemPool_t shared_pool);
 template <class T>
 inline int dalloc(cleora_ctx* ctx, T** p, size_t count) {
     return dalloc_bytes(ctx, reinterpret_cast<void**>(p), count * sizeof(T));

@@ -13,9 +13,12 @@
 // slot; and every short job runs on a high-priority stream.
 //
 // A job runs the whole method on a stream of its slot (upload and build, init, iterations,
-// FP32 result to host), so jobs on different slots overlap on the GPU.  When a job ends its slot frees the graph, trims its pool back to the driver down
-// to a small per-slot cache (charged to the budget up front), and returns the reservation;
-// waiting workers are woken and admission runs again.
+// FP32 result to host), so jobs on different slots overlap on the GPU.  The slots' contexts
+// allocate from one stream-ordered pool that keeps freed blocks: a job reuses the memory of
+// jobs before it, and no job returns memory to the driver or maps new memory once the pool
+// has grown to the working set.  When a job ends its slot frees what it held (the frees are
+// complete before the slot takes another job) and returns the reservation; waiting workers
+// are woken and admission runs again.
 //
 // Waits are bounded where a caller waits: cleora_serve_poll uses a timed condition wait.
 // Failures are per job (status in its result); the server keeps running.  The allocation
@@ -24,6 +27,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -74,7 +78,7 @@ struct cleora_server {
     int64_t reserved_short = 0;
     double short_s = 0.02;      // service estimate at or below which a job is short
     std::vector<cudaStream_t> hi, lo;  // per slot: high- and low-priority streams
-    int64_t slot_cache = 0;  // device bytes each slot's pool may keep between jobs
+    cudaMemPool_t pool = nullptr;  // shared by the slots' contexts
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work;  // workers: a job arrived or memory was returned
@@ -185,7 +189,6 @@ void worker_main(cleora_server* s, int slot) {
             DeviceGuard guard(ctx->device);
             ctx_release_all(ctx);
             cudaStreamSynchronize(ctx->stream);
-            cudaMemPoolTrimTo(ctx->pool, (size_t)s->slot_cache);
             cudaGetLastError();
         }
         {
@@ -263,12 +266,22 @@ int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
             return CLEORA_ERR_CUDA;
         }
         const int64_t total = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes : (int64_t)(free_b / 10 * 8);
-        // each slot keeps up to slot_cache bytes of its pool between jobs (small jobs then
-        // reuse it without new mappings); those bytes come out of the budget, and so does the
-        // short slots' reserve (2 GiB each, at most an eighth of the total)
-        s->slot_cache = std::min<int64_t>((int64_t)1 << 30, total / (8 * (int64_t)all_slots));
+        // the short slots' reserve (2 GiB each, at most an eighth of the total) is set aside
         s->short_budget = std::min<int64_t>(total / 8, (int64_t)s->cfg.short_slots << 31);
-        s->budget = total - s->slot_cache * all_slots - s->short_budget;
+        s->budget = total - s->short_budget;
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = cfg->device;
+        if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return CLEORA_ERR_CUDA;
+        }
+        uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool for the next jobs
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     int lo_prio = 0, hi_prio = 0;  // numerically lower is higher priority
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
@@ -286,13 +299,14 @@ int cleora_serve_create(cleora_server** out, const cleora_server_config* cfg) {
         s->hi.push_back(h);
         s->lo.push_back(l);
         cleora_ctx* c = nullptr;
-        rc = cleora_create(&c, cfg->device, l);
+        rc = ctx_create(&c, cfg->device, l, s->pool);
         if (rc == CLEORA_OK) s->slots.push_back(c);
     }
     if (rc != CLEORA_OK) {
         for (cleora_ctx* x : s->slots) cleora_destroy(x);
         for (cudaStream_t x : s->hi) cudaStreamDestroy(x);
         for (cudaStream_t x : s->lo) cudaStreamDestroy(x);
+        cudaMemPoolDestroy(s->pool);
         delete s;
         return rc;
     }
@@ -420,6 +434,10 @@ void cleora_serve_destroy(cleora_server* s) {
     }
     for (cudaStream_t x : s->hi) cudaStreamDestroy(x);
     for (cudaStream_t x : s->lo) cudaStreamDestroy(x);
+    if (s->pool) {
+        DeviceGuard guard(s->cfg.device);
+        cudaMemPoolDestroy(s->pool);
+    }
     delete s;
 }
 
