@@ -663,6 +663,10 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
     # (submit -> result in host memory)
     feed = np.array([r.t_submit - a for r, a in zip(results, arr)])[warm:]
     srv_lat = np.array([r.t_done - r.t_submit for r in results])[warm:]
+    # the service split by phase: upload + build, init, iterations + FP32 rows to the host
+    ph_build = np.array([r.t_built - r.t_admit for r in results])[warm:]
+    ph_init = np.array([r.t_inited - r.t_built for r in results])[warm:]
+    ph_iter = np.array([r.t_done - r.t_inited for r in results])[warm:]
     span = max(r.t_done for r in results[warm:]) - arr[warm]
     work = sum(r.nnz * j[1] * j[2] for r, j in zip(results[warm:], jobs[warm:]))
     big = np.array([pool[j[0]]["n"] * j[1] for j in jobs])[warm:]
@@ -682,7 +686,10 @@ def serve_measure(device, n_jobs=2000, n_capacity=600, warm=100, slots=8, seed=0
                             "feeder_wait_p99_ms": float(np.percentile(feed[cls == c], 99) * 1e3),
                             "server_latency_p99_ms": float(np.percentile(srv_lat[cls == c], 99) * 1e3),
                             "service_p50_ms": float(np.percentile(svc[cls == c], 50) * 1e3),
-                            "service_p99_ms": float(np.percentile(svc[cls == c], 99) * 1e3)})
+                            "service_p99_ms": float(np.percentile(svc[cls == c], 99) * 1e3),
+                            "build_p99_ms": float(np.percentile(ph_build[cls == c], 99) * 1e3),
+                            "init_p99_ms": float(np.percentile(ph_init[cls == c], 99) * 1e3),
+                            "iterate_download_p99_ms": float(np.percentile(ph_iter[cls == c], 99) * 1e3)})
     return {"jobs": n_jobs, "warmup_jobs": warm, "slots": slots, "short_slots": short_slots,
             "short_job_s": short_job_s,
             "failed": n_jobs - len(ok),

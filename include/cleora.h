@@ -362,6 +362,7 @@ typedef struct {
     int64_t n, nnz;
     int64_t bytes_reserved;/* the admission estimate it was charged                         */
     double t_submit, t_admit, t_done;  /* seconds on the server's monotonic clock           */
+    double t_built, t_inited;  /* when its graph build and its init returned (0 if not reached) */
 } cleora_result;
 
 /* Starts the server: max_slots worker threads, each with its own context and stream, on

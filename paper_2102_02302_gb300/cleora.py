@@ -570,7 +570,8 @@ class cleora_job(ctypes.Structure):
 class cleora_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int), ("n", _I64), ("nnz", _I64),
                 ("bytes_reserved", _I64), ("t_submit", ctypes.c_double),
-                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("t_built", ctypes.c_double), ("t_inited", ctypes.c_double)]
 
 
 def _job_struct(src, dst, weights, directed, d, iters, seed, storage, out, nodes_hint):

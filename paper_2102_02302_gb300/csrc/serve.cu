@@ -114,15 +114,18 @@ bool valid_job(const cleora_job& j) {
 int run_job(cleora_server* s, cleora_ctx* ctx, Job& job) {
     const cleora_job& j = job.spec;
     int rc = cleora_graph_build(ctx, j.src, j.dst, j.weights, j.num_edges, j.directed, 0);
+    job.res.t_built = s->now();
     if (rc == CLEORA_OK) {
         cleora_num_nodes(ctx, &job.res.n);
         cleora_num_entries(ctx, &job.res.nnz);
         if (j.out && job.res.n > j.out_rows) rc = CLEORA_ERR_INVALID_ARG;
     }
-    if (rc == CLEORA_OK) rc = cleora_init(ctx, j.d, j.seed, j.storage);
+    if (rc == CLEORA_OK) {
+        rc = cleora_init(ctx, j.d, j.seed, j.storage);
+        job.res.t_inited = s->now();
+    }
     if (rc == CLEORA_OK) rc = cleora_propagate(ctx, j.iters, j.out, 0);
     if (rc == CLEORA_OK) rc = cleora_sync(ctx);
-    (void)s;
     return rc;
 }
 
