@@ -81,7 +81,7 @@ int copy_out(cleora_ctx* ctx, void* out, const void* dev, size_t bytes, int out_
 
 int check_err_flag(cleora_ctx* ctx) {
     int flag = 0;
-    CL_CUDA(ctx, read_back(ctx, &flag, ctx->err_flag, sizeof(int), ctx->stream));
+    CL_CUDA(ctx, read_back(ctx, &flag, ctx->err_flag, sizeof(int), ctx->stream, false));
     CL_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (flag) {
         CL_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->stream));
@@ -177,9 +177,21 @@ struct Bytes32 {
 __global__ void k_put_bytes(unsigned char* dst, Bytes32 v, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = v.b[i];
 }
+// Device bytes -> mapped host memory: 16-byte words when both ends and the size allow it.
+__global__ void k_read_back(unsigned char* dst, const unsigned char* src, size_t n) {
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, T = (size_t)gridDim.x * blockDim.x;
+    if ((((uintptr_t)dst | (uintptr_t)src | n) & 15) == 0) {
+        for (size_t i = t0; i < n / 16; i += T)
+            reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+    } else {
+        for (size_t i = t0; i < n; i += T) dst[i] = src[i];
+    }
+}
 }  // namespace
 
-cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s) {
+cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s,
+                      bool by_kernel) {
+    if (bytes == 0) return cudaSuccess;
     unsigned char* h = static_cast<unsigned char*>(host);
     const unsigned char* d = static_cast<const unsigned char*>(dev);
     if (!ctx->host_stage) {  // (contexts always have one; kept for safety)
@@ -188,7 +200,14 @@ cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes
     }
     do {
         const size_t c = std::min(bytes, HOST_STAGE_BYTES);
-        cudaError_t e = cudaMemcpyAsync(ctx->host_stage, d, c, cudaMemcpyDeviceToHost, s);
+        cudaError_t e;
+        if (by_kernel) {
+            k_read_back<<<(unsigned)std::min<size_t>(16, (c + 4095) / 4096), 256, 0, s>>>(ctx->host_stage_dev, d, c);
+            ctx->launches += 1;
+            e = cudaGetLastError();
+        } else {
+            e = cudaMemcpyAsync(ctx->host_stage, d, c, cudaMemcpyDeviceToHost, s);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
         memcpy(h, ctx->host_stage, c);
@@ -285,8 +304,11 @@ int ctx_create(cleora_ctx** out, int device, void* cuda_stream, cudaMemPool_t sh
             cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
         if ((rc = dalloc(ctx, &ctx->err_flag, 1)) != CLEORA_OK) break;
-        e = cudaHostAlloc((void**)&ctx->host_stage, HOST_STAGE_BYTES, cudaHostAllocDefault);
+        e = cudaHostAlloc((void**)&ctx->host_stage, HOST_STAGE_BYTES, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&ctx->host_stage_dev, ctx->host_stage, 0);
         if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
             ctx->host_stage = nullptr;
             rc = CLEORA_ERR_OOM;
             break;

@@ -99,7 +99,8 @@ struct cleora_ctx {
     int chunks_used = 0;            // cleora_chunked_embed: chunks of the last call
     int64_t chunk_peak_bytes = 0;   // ... and the pool's high-water mark during it
     int* err_flag = nullptr;  // device int, raised by kernels
-    unsigned char* host_stage = nullptr;  // pinned, cleora::HOST_STAGE_BYTES: small read-backs
+    unsigned char* host_stage = nullptr;      // pinned and mapped, cleora::HOST_STAGE_BYTES
+    unsigned char* host_stage_dev = nullptr;  // ... its device address (small read-backs)
     int64_t launches = 0;
     int64_t inject_alloc_fail = -1;  // test hook: >= 0 counts down, the allocation at 0 fails
 };
@@ -126,10 +127,16 @@ int cuda_fail(cleora_ctx* ctx, cudaError_t e, const char* what, const char* file
 // Small copies between host and device.  A copy to or from pageable host memory is staged
 // by the driver and waits behind large copies that other streams have in flight: on a GB300 an
 // 8-byte pageable read-back waited up to 90 ms behind a 16 GiB device-to-host copy on another
-// stream, against 0.015 ms through pinned memory or a kernel.  So read-backs go through the
-// context's pinned staging buffer (the copy, then a synchronize of `s`, as a pageable copy
-// would), and small values go to the device as kernel arguments.
-cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s);
+// stream, against 0.015 ms through pinned memory or a kernel.  A pinned copy still needs a copy
+// engine, which concurrent serving jobs can keep busy with large downloads, and a kernel needs
+// a free CTA slot, which other streams' persistent kernels can hold.  So a read-back between a
+// context's own kernels (the graph build's counts and flags) is a kernel that writes the bytes
+// into the context's mapped pinned staging buffer (`by_kernel`), and one after a download (the
+// error flag at a synchronize) is a copy into the same buffer; either is followed by a
+// synchronize of `s`, as a pageable copy would be.  Small values go to the device as kernel
+// arguments.
+cudaError_t read_back(cleora_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s,
+                      bool by_kernel = true);
 cudaError_t put_bytes(cleora_ctx* ctx, void* dev, const void* host, size_t bytes, cudaStream_t s);  // bytes <= 32
 
 #define CL_TRY(x)                      \
