@@ -66,7 +66,7 @@ def test_results_alone_equal_results_in_the_mix(jobs):
     for j, a, o, r in zip(jobs, alone, outs, results):
         assert r is not None and r.status == 0
         assert r.n == a.shape[0]
-        assert r.t_submit <= r.t_admit <= r.t_done
+        assert r.t_submit <= r.t_admit <= r.t_built <= r.t_inited <= r.t_done
         assert np.array_equal(o, a)
     # and every job of the mix matches the oracle (BF16 jobs from the BF16-rounded T_0)
     for j, o in zip(jobs, outs):
