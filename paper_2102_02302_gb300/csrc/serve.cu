@@ -1,6 +1,7 @@
 // Serving runtime (include/cleora.h, cleora_serve_*): a continuous-batching request loop.
 //
-// Slots.  max_slots worker threads, each owning a context (stream + memory pool).  A worker
+// Slots.  max_slots worker threads, each owning a context and two streams (high and low
+// priority); the contexts share one device memory pool (below).  A worker
 // that is free takes the waiting job with the earliest virtual finish time -- its arrival
 // plus its estimated service time (a cost model of its host transfers, graph build and
 // gathered bytes) -- among those whose estimated peak device bytes fit in the budget beside
