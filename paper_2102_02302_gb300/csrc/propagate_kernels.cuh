@@ -256,14 +256,16 @@ template <> struct EL<__nv_bfloat16> {
 
 // CHECK: verify every column index against n (a CSR that does not come from this library's
 // own build); otherwise the index is trusted.
-// Gathered vectors in flight per lane and batch.  BF16 rows of 8-byte gathers over a whole
-// warp (d = 128) run at full occupancy with 4 (latency-bound: more warps beat deeper
-// batches); every other shape keeps 8 at 4 CTAs/SM (BF16 d = 256 on the 2M-node graph:
-// 3.3 ms against 5.1 ms with 4 in flight at 6 CTAs/SM).
-template <typename ST, int VEC, int CPL, int G>
+// Gathered vectors in flight per lane and batch.  Rows of 8-byte gathers over a whole warp
+// (BF16 d = 128) run at full occupancy (latency-bound: more warps beat deeper batches): the
+// full-row unit-weight variant takes 8 and still fits the 32 registers of 8 CTAs/SM without
+// spills (2.8B-entry graph, same box: 62.38 ms against 62.87 with 4 and 64.2 with 6); the
+// others take 4 (with 8 they spill); every other shape keeps 8 at 4 CTAs/SM (BF16 d = 256 on
+// the 2M-node graph: 3.3 ms against 5.1 ms with 4 in flight at 6 CTAs/SM).
+template <typename ST, int VEC, int CPL, int G, bool HV = false, bool FR = false>
 constexpr int inflight() {
     if (Tune<ST>::INFLIGHT > 0) return Tune<ST>::INFLIGHT;
-    if (VEC == 8 && CPL == 1 && G == 32) return 4;
+    if (VEC == 8 && CPL == 1 && G == 32) return std::is_same<ST, __nv_bfloat16>::value && !HV && FR ? 8 : 4;
     // lane groups of 16-byte gathers: 8 in flight do not fit the 64 registers of 4 CTAs/SM
     if (VEC == 16 && G < 32) return 4;
     return 8;
@@ -283,7 +285,7 @@ struct Kern {
     static constexpr int W = VEC / 4;                       // 32-bit words per vector
     static constexpr int EPV = W * EL<ST>::PER_WORD;        // elements per vector
     static constexpr int P = 32 / G;                        // lane groups per warp
-    static constexpr int IN = INF > 0 ? INF : inflight<ST, VEC, CPL, G>();
+    static constexpr int IN = INF > 0 ? INF : inflight<ST, VEC, CPL, G, HV, FR>();
     static constexpr int U = CPL >= IN ? 1 : IN / CPL;  // entries per batch
 
     // Two-level sum: `v` collects at most one 32-entry window, then is added into `t`.  Every
