@@ -103,3 +103,47 @@ def test_server_config_is_checked_before_any_cuda_call():
         h = ctypes.c_void_p()
         assert lib.cleora_serve_create(ctypes.byref(h), ctypes.byref(cfg)) == pkg.CLEORA_ERR_INVALID_ARG
         assert not h.value
+
+
+def _header_structs():
+    """Field names and C types of every `typedef struct { ... } name;` in the header."""
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "cleora.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"((?:const )?\w+\s*\**)\s*(.+)", decl)
+            ctype, names = m.group(1).replace(" ", ""), m.group(2)
+            for n in names.split(","):
+                n = n.strip()
+                ptr = n.startswith("*")
+                fields.append((n.lstrip("*").strip(), ctype + ("*" if ptr else "")))
+        out[name] = fields
+    return out
+
+
+_C_SIZES = {"int": 4, "float": 4, "double": 8, "int64_t": 8, "uint64_t": 8, "cleora_dtype": 4}
+
+
+def _c_layout_size(fields):
+    off, align = 0, 1
+    for _, t in fields:
+        sz = 8 if t.endswith("*") else _C_SIZES[t.replace("const", "")]
+        off = (off + sz - 1) // sz * sz + sz
+        align = max(align, sz)
+    return (off + align - 1) // align * align
+
+
+def test_binding_structs_match_the_header():
+    """Every struct the binding mirrors has the header's fields in the header's order, and the
+    same size under the C layout rules (no device needed)."""
+    structs = _header_structs()
+    assert {"cleora_graph_desc", "cleora_server_config", "cleora_job", "cleora_result"} <= set(structs)
+    for name, fields in structs.items():
+        mirror = getattr(pkg.cleora, name)
+        assert [f[0] for f in mirror._fields_] == [f[0] for f in fields], name
+        assert ctypes.sizeof(mirror) == _c_layout_size(fields), name
